@@ -1,0 +1,186 @@
+/*
+ * bhmc.h -- C-ABI of the GB300 Barnes-Hut octree treecode for Metropolis Monte
+ * Carlo of charged systems (Z. Gan, Z. Xu, "Efficient implementation of the
+ * Barnes-Hut octree algorithm for Monte Carlo simulations of charged systems",
+ * Sci. China Math. 2013).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a bhmc_status; nothing aborts and no C++ exception
+ *    crosses this boundary.
+ *  - A context owns all its device state (charges, octree, moments, pools).
+ *    Caller buffers passed in are copied; the caller keeps their ownership.
+ *  - Work is ordered on the CUDA stream given at creation.  Calls that return a
+ *    host value synchronise that stream.
+ *  - A failure inside a kernel (pool exhausted, traversal stack overflow) is
+ *    recorded in the context and returned by the call that launched it and by
+ *    every later call (BHMC_ESTATE) until the context is destroyed.
+ *  - Charge indexing: [0, n_mobile) mobile ions, [n_mobile, n_mobile+n_fixed)
+ *    fixed charges, then (with images) the image of ion i at n_mobile+n_fixed+i.
+ *  - Lengths are in the unit of l_B; energies are beta*V (units of k_B T).
+ */
+#ifndef BHMC_H
+#define BHMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BHMC_OK = 0,
+  BHMC_EINVAL = 1,      /* invalid argument or parameter */
+  BHMC_EDOMAIN = 2,     /* a position lies outside the root cube */
+  BHMC_EOVERLAP = 3,    /* a position violates the confinement shell */
+  BHMC_ENOMEM = 4,      /* device or host allocation failed */
+  BHMC_ENOMEM_POOL = 5, /* the node pool of a context is exhausted */
+  BHMC_ECUDA = 6,       /* a CUDA runtime call failed */
+  BHMC_ETIMEOUT = 7,    /* a bounded device loop ran out of iterations */
+  BHMC_ESTATE = 8,      /* the context holds an earlier device error */
+  BHMC_ECAPACITY = 9,   /* a depth-Dmax cell would hold more than C charges */
+  BHMC_ESTACK = 10      /* a traversal stack overflowed */
+} bhmc_status;
+
+enum { BHMC_PREC_F32 = 0, BHMC_PREC_F64 = 1 };   /* traversal arithmetic */
+enum { BHMC_LAYOUT_SOA = 0, BHMC_LAYOUT_AOS = 1 }; /* FP32 moment layout */
+enum { BHMC_HOST_PTRS = 0, BHMC_DEVICE_PTRS = 1 }; /* flags: where caller arrays live */
+
+/* Outcome of one Metropolis trial move (Sec. 2 of the paper, step 2). */
+enum {
+  BHMC_ACCEPT = 0,
+  BHMC_REJECT_ENERGY = 1,   /* alpha > exp(-beta dE) */
+  BHMC_REJECT_DOMAIN = 2,   /* trial position (or its image) outside the root cube */
+  BHMC_REJECT_OVERLAP = 3,  /* trial position outside the confinement shell */
+  BHMC_REJECT_CAPACITY = 4  /* would overfill a depth-Dmax cell */
+};
+
+/* Parameters of a system.  Cites: l_B and beta, Eq. (1.1)/(2.1); theta, p and
+   N0, Sec. 3.2 and Eq. (3.3); the root cube, Sec. 3.2; the cell model, Sec. 4. */
+typedef struct {
+  double lB;          /* Bjerrum length (> 0) */
+  double beta;        /* inverse temperature of the Metropolis rule (>= 0) */
+  double theta;       /* MAC: multipole iff rho_A/|r_A - x| <= theta, 0 <= theta < 1 */
+  int32_t p;          /* Taylor truncation order; the CUDA path supports 2, 4 and 6 */
+  int32_t N0;         /* minimum expansion number (>= 0) */
+  int32_t C;          /* leaf capacity, 2..32: a cluster holding more than C charges splits */
+  int32_t Dmax;       /* deepest level, 1..20 */
+  double root_lo[3];  /* lower corner of the root cube, a multiple of side/2^Dmax */
+  double root_side;   /* side of the root cube, a power of two */
+  int32_t shell;      /* 1: mobile ions confined to shell_rmin <= |r| <= shell_rmax */
+  double shell_rmin, shell_rmax;
+  int32_t images;     /* 1: each mobile ion carries an image at R^2 r/|r|^2, charge alpha q R/|r| */
+  double image_R, image_alpha;
+  int32_t precision;  /* BHMC_PREC_F32 (FP32 traversal, FP64 moments) or BHMC_PREC_F64 (all FP64) */
+  int32_t warps;      /* warps cooperating on one move: 1, 2 or 4 (4 needs images) */
+  int32_t layout;     /* BHMC_LAYOUT_SOA or BHMC_LAYOUT_AOS for the FP32 moment mirror */
+  double node_factor; /* node pool = 64 + node_factor * charges (0 selects 2.0) */
+} bhmc_params;
+
+typedef struct bhmc_ctx bhmc_ctx;
+typedef struct bhmc_batch bhmc_batch;
+
+/* Interaction-list counters of one evaluation (equal to the oracle's). */
+typedef struct {
+  int64_t visited;  /* (cluster, evaluation point) pairs examined */
+  int64_t accepted; /* pairs evaluated by the multipole approximation */
+  int64_t pairs;    /* particle-particle direct terms */
+  int64_t mac_fp64; /* MAC decisions settled by the exact FP64 test */
+} bhmc_counters;
+
+/* One trial move of a Monte Carlo run. */
+typedef struct {
+  int64_t i;        /* chosen mobile ion */
+  double r_new[3];  /* trial position */
+  double dE;        /* energy difference (0 if rejected before evaluation) */
+  int32_t outcome;  /* BHMC_ACCEPT or BHMC_REJECT_* */
+  int32_t flagged;  /* 1 if |beta dE + ln alpha| < 1e-6 (decision near the threshold) */
+} bhmc_move_record;
+
+typedef struct {
+  int64_t moves, accepted, rej_energy, rej_domain, rej_overlap, rej_capacity, flagged;
+  double energy;    /* running energy: sum of accepted dE since creation or bhmc_set_energy */
+} bhmc_mc_stats;
+
+const char* bhmc_status_string(bhmc_status s);
+
+/* Build the octree of n_mobile + n_fixed charges (Sec. 3.2: the root cube is
+   bisected recursively; a cluster holding more than C charges is split until
+   level Dmax) and the FP64 moments M_A^n = sum_j q_j (r_j - r_A)^n of Eq. (3.3).
+   q[n], xyz[3n] (x,y,z interleaved), host or device memory per `flags`,
+   copied.  cuda_stream: a cudaStream_t or NULL for the default stream.
+   Errors: EINVAL (parameters), EDOMAIN (charge or image outside the root),
+   EOVERLAP (ion outside the shell), ECAPACITY, ENOMEM, ECUDA. */
+bhmc_status bhmc_create(const bhmc_params* params, int64_t n_mobile, int64_t n_fixed,
+                        const double* q, const double* xyz, int32_t flags, void* cuda_stream,
+                        bhmc_ctx** out);
+bhmc_status bhmc_destroy(bhmc_ctx* ctx);
+
+/* Number of charges in the tree (ions, fixed charges and images). */
+bhmc_status bhmc_n_charges(const bhmc_ctx* ctx, int64_t* n);
+/* Copy current charges and positions (xyz interleaved) to host or device buffers. */
+bhmc_status bhmc_get_charges(bhmc_ctx* ctx, double* q, double* xyz, int32_t flags);
+
+/* Energy difference of moving mobile ion i (and its image) to r_new (Sec. 1:
+   V_i evaluated before and after the displacement; Sec. 3.2 traversal with the
+   multipole approximation of Eq. (3.3)); the state is not modified.  The moved
+   charges are excluded from the pre-move tree.  Returns EDOMAIN/EOVERLAP when
+   the trial position would be rejected before any evaluation.  counters may be
+   NULL. */
+bhmc_status bhmc_delta_energy(bhmc_ctx* ctx, int64_t i, const double r_new[3], double* dE,
+                              bhmc_counters* counters);
+
+/* Local adjustment of Sec. 3.3 for a move of ion i (and its image) to r_new,
+   applied unconditionally: remove from the old leaf (swap with the last slot),
+   insert into the new one, update counts and FP64 moments on both ancestor
+   paths, merge/split clusters so the tree stays the canonical tree of the
+   particle set.  Errors: EDOMAIN, EOVERLAP, ECAPACITY (state unchanged),
+   ENOMEM_POOL. */
+bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]);
+
+/* n_moves Metropolis trials (Sec. 2), one kernel launch per trial.  Trial m
+   uses Philox4x32-10 with key (seed) and counter (m, 0, 0) for the ion index
+   and displacement (uniform in [-step/2, step/2)^3) and counter (m, 0, 1) for
+   alpha; m runs from move0.  stats must not be NULL; records (host, n_moves
+   entries) may be NULL. */
+bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed,
+                         uint64_t move0, bhmc_mc_stats* stats, bhmc_move_record* records);
+
+/* Running energy (sum of accepted dE since creation, or rebased by set). */
+bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E);
+bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);
+
+/* Total treecode energy E = (1/2) l_B sum_i q_i phi_tree(r_i), every charge
+   excluded from its own sum (Eq. 1.1 evaluated by the Sec. 3.2 traversal). */
+bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E);
+/* Total energy by direct O(N^2) summation of Eq. (1.1) on the GPU (FP64). */
+bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E);
+
+/* Tree export for parity checks.  rows[4*k..4*k+3] = (depth, Morton key with a
+   leading 1 bit, is_leaf, count) in depth-first order (children in octant
+   order); members receives every leaf's charge indices (sorted) in row order.
+   moments (may be NULL) receives the FP64 moments, K(p) per row.  *n_rows is
+   the number of rows written.  EINVAL if a buffer is too small. */
+bhmc_status bhmc_export_tree(bhmc_ctx* ctx, int64_t* rows, int64_t max_rows, int64_t* members,
+                             int64_t max_members, double* moments, int64_t* n_rows);
+
+/* ---- batches of independent replicas (one octree each) ---- */
+
+/* n_rep systems sharing one parameter set; replica r has n_mobile[r] ions and
+   n_fixed[r] fixed charges with arrays q[r], xyz[r]. */
+bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const int64_t* n_mobile,
+                              const int64_t* n_fixed, const double* const* q,
+                              const double* const* xyz, int32_t flags, void* cuda_stream,
+                              bhmc_batch** out);
+bhmc_status bhmc_batch_destroy(bhmc_batch* batch);
+/* Borrowed context of replica r (valid until the batch is destroyed; do not destroy it). */
+bhmc_status bhmc_batch_replica(bhmc_batch* batch, int32_t r, bhmc_ctx** ctx);
+/* n_moves Metropolis trials on every replica in ONE persistent kernel launch,
+   replayed from a CUDA graph.  Replica r uses key seeds[r] and counter
+   (m, r, tag).  stats: n_rep entries (may be NULL). */
+bhmc_status bhmc_batch_step_mc(bhmc_batch* batch, uint64_t n_moves, double step,
+                               const uint64_t* seeds, uint64_t move0, bhmc_mc_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,387 @@
+"""ctypes binding of libbhmc.so (the C-ABI of include/bhmc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The module-level functions carry the C names; ``Context`` and ``Batch`` are
+thin owners of the handles.  Arrays may be numpy (host) or torch CUDA tensors
+(device pointers, passed with BHMC_DEVICE_PTRS); the CUDA stream is torch's
+current stream when torch is available.  If the library is missing this module
+raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, EDOMAIN, EOVERLAP, ENOMEM, ENOMEM_POOL, ECUDA, ETIMEOUT, ESTATE, ECAPACITY, ESTACK = range(11)
+PREC_F32, PREC_F64 = 0, 1
+LAYOUT_SOA, LAYOUT_AOS = 0, 1
+HOST_PTRS, DEVICE_PTRS = 0, 1
+ACCEPT, REJECT_ENERGY, REJECT_DOMAIN, REJECT_OVERLAP, REJECT_CAPACITY = range(5)
+
+
+class BhmcError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, bhmc_status_string(status), status))
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("lB", C.c_double), ("beta", C.c_double), ("theta", C.c_double),
+        ("p", C.c_int32), ("N0", C.c_int32), ("C", C.c_int32), ("Dmax", C.c_int32),
+        ("root_lo", C.c_double * 3), ("root_side", C.c_double),
+        ("shell", C.c_int32), ("shell_rmin", C.c_double), ("shell_rmax", C.c_double),
+        ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
+        ("precision", C.c_int32), ("warps", C.c_int32), ("layout", C.c_int32),
+        ("node_factor", C.c_double),
+    ]
+
+
+class Counters(C.Structure):
+    _fields_ = [("visited", C.c_int64), ("accepted", C.c_int64), ("pairs", C.c_int64),
+                ("mac_fp64", C.c_int64)]
+
+
+class McStats(C.Structure):
+    _fields_ = [("moves", C.c_int64), ("accepted", C.c_int64), ("rej_energy", C.c_int64),
+                ("rej_domain", C.c_int64), ("rej_overlap", C.c_int64), ("rej_capacity", C.c_int64),
+                ("flagged", C.c_int64), ("energy", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+RECORD_DTYPE = np.dtype([("i", "<i8"), ("r_new", "<f8", (3,)), ("dE", "<f8"), ("outcome", "<i4"),
+                         ("flagged", "<i4")])
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+
+
+def lib():
+    """Open libbhmc.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libbhmc.so is not built (run __graft_entry__.build()); "
+                               "the CUDA library is required, there is no CPU fallback")
+        L = C.CDLL(_build.LIB)
+        st = C.c_int
+        L.bhmc_status_string.argtypes = [st]
+        L.bhmc_status_string.restype = C.c_char_p
+        L.bhmc_create.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.bhmc_destroy.argtypes = [C.c_void_p]
+        L.bhmc_n_charges.argtypes = [C.c_void_p, _i64p]
+        L.bhmc_get_charges.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+        L.bhmc_delta_energy.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, C.POINTER(Counters)]
+        L.bhmc_commit_move.argtypes = [C.c_void_p, C.c_int64, _dp]
+        L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
+                                   C.POINTER(McStats), C.c_void_p]
+        L.bhmc_get_energy.argtypes = [C.c_void_p, _dp]
+        L.bhmc_set_energy.argtypes = [C.c_void_p, C.c_double]
+        L.bhmc_energy.argtypes = [C.c_void_p, _dp]
+        L.bhmc_energy_direct.argtypes = [C.c_void_p, _dp]
+        L.bhmc_export_tree.argtypes = [C.c_void_p, _i64p, C.c_int64, _i64p, C.c_int64, _dp, _i64p]
+        L.bhmc_batch_create.argtypes = [C.c_int32, C.POINTER(Params), _i64p, _i64p,
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                        C.c_void_p, C.POINTER(C.c_void_p)]
+        L.bhmc_batch_destroy.argtypes = [C.c_void_p]
+        L.bhmc_batch_replica.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]
+        L.bhmc_batch_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
+                                         C.c_uint64, C.POINTER(McStats)]
+        _lib = L
+    return _lib
+
+
+def bhmc_status_string(status: int) -> str:
+    try:
+        return lib().bhmc_status_string(status).decode()
+    except Exception:  # library not loadable: still describe the code
+        return "status %d" % status
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise BhmcError(rc, what)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+def make_params(d: dict, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_factor=0.0) -> Params:
+    P = Params()
+    P.lB = d.get("lB", 1.0)
+    P.beta = d.get("beta", 1.0)
+    P.theta = d["theta"]
+    P.p = d["p"]
+    P.N0 = d.get("N0", 0)
+    P.C = d["C"]
+    P.Dmax = d["Dmax"]
+    for a in range(3):
+        P.root_lo[a] = d["root_lo"][a]
+    P.root_side = d["root_side"]
+    P.shell = 1 if d.get("shell") else 0
+    P.shell_rmin, P.shell_rmax = d["shell"] if d.get("shell") else (0.0, 0.0)
+    P.images = 1 if d.get("image") else 0
+    P.image_R, P.image_alpha = d["image"] if d.get("image") else (0.0, 0.0)
+    P.precision = d.get("precision", precision)
+    P.warps = d.get("warps", warps)
+    P.layout = d.get("layout", layout)
+    P.node_factor = d.get("node_factor", node_factor)
+    return P
+
+
+def _ptr_and_flag(a):
+    """(pointer, flags, keepalive) for a numpy array or a torch CUDA tensor of float64."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64:
+                raise TypeError("float64 tensors required")
+            a = a.contiguous()
+            return C.c_void_p(a.data_ptr()), (DEVICE_PTRS if a.is_cuda else HOST_PTRS), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return C.c_void_p(a.ctypes.data), HOST_PTRS, a
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def bhmc_create(params: Params, n_mobile: int, n_fixed: int, q, xyz, stream=None):
+    qp, f1, kq = _ptr_and_flag(q)
+    xp, f2, kx = _ptr_and_flag(xyz)
+    if f1 != f2:
+        raise ValueError("q and xyz must both be host or both device arrays")
+    h = C.c_void_p()
+    _check(lib().bhmc_create(C.byref(params), n_mobile, n_fixed, qp, xp, f1, _stream(stream),
+                             C.byref(h)), "bhmc_create")
+    return h
+
+
+def bhmc_destroy(h):
+    _check(lib().bhmc_destroy(h), "bhmc_destroy")
+
+
+def bhmc_delta_energy(h, i, r_new):
+    b = (C.c_double * 3)(*[float(v) for v in r_new])
+    dE = C.c_double()
+    cnt = Counters()
+    rc = lib().bhmc_delta_energy(h, int(i), b, C.byref(dE), C.byref(cnt))
+    return rc, dE.value, cnt
+
+
+def bhmc_commit_move(h, i, r_new):
+    b = (C.c_double * 3)(*[float(v) for v in r_new])
+    return lib().bhmc_commit_move(h, int(i), b)
+
+
+def bhmc_step_mc(h, n_moves, step, seed, move0=0, records=False):
+    st = McStats()
+    rec = np.zeros(n_moves, dtype=RECORD_DTYPE) if records else None
+    rp = C.c_void_p(rec.ctypes.data) if records and n_moves else C.c_void_p(0)
+    _check(lib().bhmc_step_mc(h, n_moves, step, seed, move0, C.byref(st), rp), "bhmc_step_mc")
+    return st, rec
+
+
+def bhmc_energy(h):
+    e = C.c_double()
+    _check(lib().bhmc_energy(h, C.byref(e)), "bhmc_energy")
+    return e.value
+
+
+def bhmc_energy_direct(h):
+    e = C.c_double()
+    _check(lib().bhmc_energy_direct(h, C.byref(e)), "bhmc_energy_direct")
+    return e.value
+
+
+def bhmc_get_energy(h):
+    e = C.c_double()
+    _check(lib().bhmc_get_energy(h, C.byref(e)), "bhmc_get_energy")
+    return e.value
+
+
+def bhmc_set_energy(h, E):
+    _check(lib().bhmc_set_energy(h, float(E)), "bhmc_set_energy")
+
+
+def bhmc_n_charges(h):
+    n = C.c_int64()
+    _check(lib().bhmc_n_charges(h, C.byref(n)), "bhmc_n_charges")
+    return n.value
+
+
+def bhmc_get_charges(h):
+    n = bhmc_n_charges(h)
+    q = np.zeros(n)
+    x = np.zeros((n, 3))
+    _check(lib().bhmc_get_charges(h, C.c_void_p(q.ctypes.data), C.c_void_p(x.ctypes.data), HOST_PTRS),
+           "bhmc_get_charges")
+    return q, x
+
+
+def bhmc_export_tree(h, K=None):
+    """{(depth, key): (is_leaf, count, members or None)} and, if K is given, moments per key."""
+    n = bhmc_n_charges(h)
+    cap = 8 * n + 1024
+    rows = np.zeros((cap, 4), dtype=np.int64)
+    mem = np.zeros(n + 8, dtype=np.int64)
+    M = np.zeros((cap, K)) if K else None
+    nr = C.c_int64()
+    _check(lib().bhmc_export_tree(h, rows.ctypes.data_as(_i64p), cap, mem.ctypes.data_as(_i64p), len(mem),
+                                  M.ctypes.data_as(_dp) if K else None, C.byref(nr)), "bhmc_export_tree")
+    tree, moms = {}, {}
+    off = 0
+    for r in range(nr.value):
+        d, k, leaf, cnt = (int(v) for v in rows[r])
+        members = None
+        if leaf:
+            members = tuple(int(v) for v in mem[off:off + cnt])
+            off += cnt
+        tree[(d, k)] = (bool(leaf), cnt, members)
+        if K:
+            moms[(d, k)] = M[r].copy()
+    return (tree, moms) if K else tree
+
+
+def bhmc_batch_create(params: Params, systems, stream=None):
+    n = len(systems)
+    nm = (C.c_int64 * n)(*[s["n_mobile"] for s in systems])
+    nf = (C.c_int64 * n)(*[s["n_fixed"] for s in systems])
+    keep = []
+    qs = (C.c_void_p * n)()
+    xs = (C.c_void_p * n)()
+    flag = None
+    for r, s in enumerate(systems):
+        qp, f1, kq = _ptr_and_flag(s["q"])
+        xp, f2, kx = _ptr_and_flag(s["xyz"])
+        if flag is None:
+            flag = f1
+        if f1 != flag or f2 != flag:
+            raise ValueError("all arrays must be host or all device")
+        keep += [kq, kx]
+        qs[r] = qp.value
+        xs[r] = xp.value
+    h = C.c_void_p()
+    _check(lib().bhmc_batch_create(n, C.byref(params), nm, nf, qs, xs, flag, _stream(stream), C.byref(h)),
+           "bhmc_batch_create")
+    return h
+
+
+def bhmc_batch_destroy(h):
+    _check(lib().bhmc_batch_destroy(h), "bhmc_batch_destroy")
+
+
+def bhmc_batch_replica(h, r):
+    c = C.c_void_p()
+    _check(lib().bhmc_batch_replica(h, r, C.byref(c)), "bhmc_batch_replica")
+    return c
+
+
+def bhmc_batch_step_mc(h, n_rep, n_moves, step, seeds, move0=0):
+    sd = (C.c_uint64 * n_rep)(*[int(s) for s in seeds])
+    st = (McStats * n_rep)()
+    _check(lib().bhmc_batch_step_mc(h, n_moves, step, sd, move0, st), "bhmc_batch_step_mc")
+    return [s.as_dict() for s in st]
+
+
+# ------------------------------------------------------------------ owners
+class Context:
+    """One system and its device-resident octree."""
+
+    def __init__(self, workload: dict, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_factor=0.0,
+                 stream=None, _handle=None):
+        self.params = make_params(workload["params"], precision, warps, layout, node_factor)
+        self.K = (self.params.p + 1) * (self.params.p + 2) * (self.params.p + 3) // 6
+        self.n_mobile = workload["n_mobile"]
+        self.n_fixed = workload["n_fixed"]
+        self._owned = _handle is None
+        self.h = _handle if _handle is not None else bhmc_create(
+            self.params, self.n_mobile, self.n_fixed, workload["q"], workload["xyz"], stream)
+
+    def close(self):
+        if self._owned and self.h:
+            bhmc_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def delta_energy(self, i, r_new):
+        return bhmc_delta_energy(self.h, i, r_new)
+
+    def commit_move(self, i, r_new):
+        return bhmc_commit_move(self.h, i, r_new)
+
+    def step_mc(self, n_moves, step, seed, move0=0, records=False):
+        return bhmc_step_mc(self.h, n_moves, step, seed, move0, records)
+
+    def energy(self):
+        return bhmc_energy(self.h)
+
+    def energy_direct(self):
+        return bhmc_energy_direct(self.h)
+
+    def get_energy(self):
+        return bhmc_get_energy(self.h)
+
+    def set_energy(self, E):
+        bhmc_set_energy(self.h, E)
+
+    def charges(self):
+        return bhmc_get_charges(self.h)
+
+    def export_tree(self, moments=False):
+        return bhmc_export_tree(self.h, self.K if moments else None)
+
+
+class Batch:
+    """Independent replicas, each with its own octree, stepped in one persistent launch."""
+
+    def __init__(self, systems, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_factor=0.0, stream=None):
+        self.params = make_params(systems[0]["params"], precision, warps, layout, node_factor)
+        self.n = len(systems)
+        self.systems = systems
+        self.h = bhmc_batch_create(self.params, systems, stream)
+
+    def replica(self, r) -> Context:
+        c = Context.__new__(Context)
+        c.params = self.params
+        c.K = (self.params.p + 1) * (self.params.p + 2) * (self.params.p + 3) // 6
+        c.n_mobile = self.systems[r]["n_mobile"]
+        c.n_fixed = self.systems[r]["n_fixed"]
+        c._owned = False
+        c.h = bhmc_batch_replica(self.h, r)
+        return c
+
+    def step_mc(self, n_moves, step, seeds, move0=0):
+        return bhmc_batch_step_mc(self.h, self.n, n_moves, step, seeds, move0)
+
+    def close(self):
+        if self.h:
+            bhmc_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

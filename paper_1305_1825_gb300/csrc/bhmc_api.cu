@@ -1,0 +1,763 @@
+// bhmc_api.cu -- host side of the C-ABI declared in include/bhmc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bhmc_build.cuh"
+#include "bhmc_launch.cuh"
+
+namespace bhmc {
+struct DeltaOut {
+  double dE;
+  long long cnt[4];
+  int status;
+  int err;
+};
+struct MoveRec {
+  long long i;
+  double r[3];
+  double dE;
+  int outcome, flagged;
+};
+struct BatchArgs {
+  unsigned long long n_moves, move0;
+  double step;
+  const unsigned long long* seeds;
+};
+}  // namespace bhmc
+
+using namespace bhmc;
+
+static_assert(sizeof(MoveRec) == sizeof(bhmc_move_record), "record layout");
+
+struct bhmc_ctx {
+  bhmc_params P;
+  SysDev S;
+  cudaStream_t stream = nullptr;
+  void* arena = nullptr;
+  void* io = nullptr;       // device scratch for small results
+  void* io_host = nullptr;  // pinned mirror
+  int sticky = 0;
+  bool borrowed = false;
+};
+
+struct bhmc_batch {
+  std::vector<bhmc_ctx*> reps;
+  SysDev* d_views = nullptr;
+  BatchArgs* d_args = nullptr;
+  BatchArgs* h_args = nullptr;
+  unsigned long long* d_seeds = nullptr;
+  int* d_next = nullptr;
+  bhmc_mc_stats* d_stats = nullptr;
+  bhmc_mc_stats* h_stats = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int grid = 0;
+  int warps = 1;
+  int p = 4;
+};
+
+#define CK(call)                              \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return BHMC_ECUDA; \
+  } while (0)
+
+const char* bhmc_status_string(bhmc_status s) {
+  switch (s) {
+    case BHMC_OK: return "ok";
+    case BHMC_EINVAL: return "invalid argument";
+    case BHMC_EDOMAIN: return "position outside the root cube";
+    case BHMC_EOVERLAP: return "position outside the confinement shell";
+    case BHMC_ENOMEM: return "out of memory";
+    case BHMC_ENOMEM_POOL: return "node pool exhausted";
+    case BHMC_ECUDA: return "CUDA error";
+    case BHMC_ETIMEOUT: return "bounded device loop exhausted";
+    case BHMC_ESTATE: return "context holds an earlier device error";
+    case BHMC_ECAPACITY: return "depth-Dmax cell over capacity";
+    case BHMC_ESTACK: return "traversal stack overflow";
+  }
+  return "unknown status";
+}
+
+static bool pow2(double v) {
+  int e;
+  return v > 0.0 && std::frexp(v, &e) == 0.5;
+}
+
+static bhmc_status validate(const bhmc_params* P) {
+  if (!P) return BHMC_EINVAL;
+  if (!(P->lB > 0.0) || !(P->beta >= 0.0) || !(P->theta >= 0.0 && P->theta < 1.0)) return BHMC_EINVAL;
+  if (P->p != 2 && P->p != 4 && P->p != 6) return BHMC_EINVAL;
+  if (P->N0 < 0 || P->C < 2 || P->C > BHMC_MAX_C || P->Dmax < 1 || P->Dmax > BHMC_MAX_D) return BHMC_EINVAL;
+  if (!pow2(P->root_side)) return BHMC_EINVAL;
+  const double hmin = std::ldexp(P->root_side, -P->Dmax);
+  for (int a = 0; a < 3; ++a) {
+    const double c = P->root_lo[a] / hmin;
+    if (!std::isfinite(c) || c != std::floor(c)) return BHMC_EINVAL;
+    // every cluster centre must be exact in FP32: |centre| / (hmin/2) < 2^24
+    const double far = (std::fabs(P->root_lo[a]) + P->root_side) / (0.5 * hmin);
+    if (far >= 16777216.0) return BHMC_EINVAL;
+  }
+  if (P->shell && !(P->shell_rmin >= 0.0 && P->shell_rmax >= P->shell_rmin)) return BHMC_EINVAL;
+  if (P->images && !(P->image_R > 0.0)) return BHMC_EINVAL;
+  if (P->precision != BHMC_PREC_F32 && P->precision != BHMC_PREC_F64) return BHMC_EINVAL;
+  if (P->layout != BHMC_LAYOUT_SOA && P->layout != BHMC_LAYOUT_AOS) return BHMC_EINVAL;
+  if (P->warps != 1 && P->warps != 2 && P->warps != 4) return BHMC_EINVAL;
+  if (P->node_factor < 0.0) return BHMC_EINVAL;
+  return BHMC_OK;
+}
+
+template <typename T>
+static T* carve(char*& cur, size_t n) {
+  T* p = reinterpret_cast<T*>(cur);
+  cur += (n * sizeof(T) + 255) & ~size_t(255);
+  return p;
+}
+
+static size_t arena_bytes(const SysDev& S) {
+  size_t b = 0;
+  auto add = [&](size_t n) { b += (n + 255) & ~size_t(255); };
+  add(4 * sizeof(double) * S.n_tot);  // px py pz pq
+  add(sizeof(unsigned long long) * S.n_tot);
+  add(2 * sizeof(int) * S.n_tot);
+  add(sizeof(float4) * S.node_cap);
+  add(sizeof(int4) * S.node_cap);
+  add(sizeof(float) * (size_t)S.node_cap * S.Kp);
+  add(sizeof(double) * (size_t)S.node_cap * S.K);
+  add(2 * sizeof(float4) * (size_t)S.node_cap * (S.C + 2));
+  add(sizeof(int) * 2);
+  add(sizeof(int) * S.group_cap);
+  add(sizeof(double));
+  add(sizeof(int));
+  return b + 16 * 256;
+}
+
+static void carve_all(SysDev& S, char* base) {
+  char* cur = base;
+  S.px = carve<double>(cur, S.n_tot);
+  S.py = carve<double>(cur, S.n_tot);
+  S.pz = carve<double>(cur, S.n_tot);
+  S.pq = carve<double>(cur, S.n_tot);
+  S.ckey = carve<unsigned long long>(cur, S.n_tot);
+  S.leaf_of = carve<int>(cur, S.n_tot);
+  S.slot_of = carve<int>(cur, S.n_tot);
+  S.nA = carve<float4>(cur, S.node_cap);
+  S.nB = carve<int4>(cur, S.node_cap);
+  S.M32 = carve<float>(cur, (size_t)S.node_cap * S.Kp);
+  S.M64 = carve<double>(cur, (size_t)S.node_cap * S.K);
+  S.sA = carve<float4>(cur, (size_t)S.node_cap * (S.C + 2));
+  S.sB = carve<float4>(cur, (size_t)S.node_cap * (S.C + 2));
+  S.pool = carve<int>(cur, 2);
+  S.free_list = carve<int>(cur, S.group_cap);
+  S.energy = carve<double>(cur, 1);
+  S.err = carve<int>(cur, 1);
+}
+
+static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_fix) {
+  std::memset(&S, 0, sizeof(S));
+  S.n_mob = (int)n_mob;
+  S.n_fix = (int)n_fix;
+  S.n_tot = (int)(n_mob + n_fix + (P->images ? n_mob : 0));
+  S.p = P->p;
+  S.K = nterms(P->p);
+  S.Kp = pad4(S.K);
+  S.N0 = P->N0;
+  S.C = P->C;
+  S.Dmax = P->Dmax;
+  S.images = P->images ? 1 : 0;
+  S.shell = P->shell ? 1 : 0;
+  S.prec = P->precision;
+  S.layout = P->layout;
+  S.lB = P->lB;
+  S.beta = P->beta;
+  S.theta2 = P->theta * P->theta;
+  S.theta2f = (float)S.theta2;
+  S.lBf = (float)P->lB;
+  S.root_side = P->root_side;
+  S.inv_hmin = std::ldexp(1.0, P->Dmax) / P->root_side;
+  for (int a = 0; a < 3; ++a) {
+    S.root_lo[a] = P->root_lo[a];
+    S.root_cell[a] = (long long)(P->root_lo[a] * S.inv_hmin);
+  }
+  S.rmin = P->shell_rmin;
+  S.rmax = P->shell_rmax;
+  S.img_R = P->image_R;
+  S.img_alpha = P->image_alpha;
+  const double f = P->node_factor > 0.0 ? P->node_factor : (1.0 + std::max(1.0, 8.0 / P->C));
+  long long cap = 64 + (long long)std::ceil(f * (double)S.n_tot);
+  cap = (cap + 7) & ~7LL;
+  S.node_cap = (int)std::min<long long>(cap, (1LL << 28));
+  S.group_cap = S.node_cap / 8;
+}
+
+static bhmc_status ctx_check(bhmc_ctx* c) {
+  if (!c) return BHMC_EINVAL;
+  if (c->sticky) return BHMC_ESTATE;
+  return BHMC_OK;
+}
+
+// Read the device error word; latch it.
+static bhmc_status sync_err(bhmc_ctx* c) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    c->sticky = BHMC_ECUDA;
+    return BHMC_ECUDA;
+  }
+  int e = 0;
+  if (cudaMemcpy(&e, c->S.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    c->sticky = BHMC_ECUDA;
+    return BHMC_ECUDA;
+  }
+  if (e) {
+    c->sticky = e;
+    return (bhmc_status)e;
+  }
+  return BHMC_OK;
+}
+
+static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, int32_t flags) {
+  SysDev& S = c->S;
+  cudaStream_t st = c->stream;
+  const int n_in = S.n_mob + S.n_fix;
+  double *dq = nullptr, *dx = nullptr;
+  int *perm = nullptr, *perm2 = nullptr, *seg = nullptr, *la = nullptr, *lb = nullptr, *fl = nullptr,
+      *dflags = nullptr;
+  bhmc_status rc = BHMC_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    if (!(flags & BHMC_DEVICE_PTRS)) {
+      cudaFree(dq);
+      cudaFree(dx);
+    }
+    cudaFree(perm);
+    cudaFree(perm2);
+    cudaFree(seg);
+    cudaFree(la);
+    cudaFree(lb);
+    cudaFree(fl);
+    cudaFree(dflags);
+  };
+  if (flags & BHMC_DEVICE_PTRS) {
+    dq = const_cast<double*>(q);
+    dx = const_cast<double*>(xyz);
+  } else {
+    if (cudaMalloc(&dq, sizeof(double) * n_in) != cudaSuccess ||
+        cudaMalloc(&dx, sizeof(double) * 3 * n_in) != cudaSuccess) {
+      cleanup();
+      return BHMC_ENOMEM;
+    }
+    if (cudaMemcpyAsync(dq, q, sizeof(double) * n_in, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dx, xyz, sizeof(double) * 3 * n_in, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cleanup();
+      return BHMC_ECUDA;
+    }
+  }
+  if (cudaMalloc(&perm, sizeof(int) * S.n_tot) != cudaSuccess ||
+      cudaMalloc(&perm2, sizeof(int) * S.n_tot) != cudaSuccess ||
+      cudaMalloc(&seg, sizeof(int) * S.node_cap) != cudaSuccess ||
+      cudaMalloc(&la, sizeof(int) * S.node_cap) != cudaSuccess ||
+      cudaMalloc(&lb, sizeof(int) * S.node_cap) != cudaSuccess ||
+      cudaMalloc(&fl, sizeof(int) * S.node_cap) != cudaSuccess ||
+      cudaMalloc(&dflags, sizeof(int) * 8) != cudaSuccess) {
+    cleanup();
+    return BHMC_ENOMEM;
+  }
+  int hflags[8] = {0};
+  bool ok = cudaMemsetAsync(dflags, 0, sizeof(int) * 8, st) == cudaSuccess &&
+            build_init_charges(S, dq, dx, dflags, st) == cudaSuccess &&
+            build_keys(S, perm, dflags, st) == cudaSuccess && build_root(S, seg, st) == cudaSuccess &&
+            cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    cleanup();
+    return BHMC_ECUDA;
+  }
+  if (hflags[0]) rc = BHMC_EDOMAIN;
+  else if (hflags[1]) rc = BHMC_EOVERLAP;
+  if (rc != BHMC_OK) {
+    cleanup();
+    return rc;
+  }
+  int n_list = (S.n_tot > S.C && S.Dmax > 0) ? 1 : 0;
+  int zero = 0;
+  if (cudaMemcpyAsync(la, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cleanup();
+    return BHMC_ECUDA;
+  }
+  int groups = 1;
+  int* dcount = dflags + 4;
+  for (int depth = 0; n_list > 0; ++depth) {
+    if (groups + n_list > S.group_cap) {
+      cleanup();
+      return BHMC_ENOMEM_POOL;
+    }
+    if (build_split_level(S, la, n_list, groups, depth, perm, perm2, seg, fl, st) != cudaSuccess ||
+        build_compact(fl, 8 * n_list, lb, dcount, st) != cudaSuccess) {
+      cleanup();
+      return BHMC_ECUDA;
+    }
+    groups += n_list;
+    if (cudaMemcpyAsync(&n_list, dcount, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cleanup();
+      return BHMC_ECUDA;
+    }
+    std::swap(la, lb);
+  }
+  if (cudaMemcpyAsync(S.pool, &groups, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      build_leaves_moments(S, 8 * groups, perm, seg, dflags, st) != cudaSuccess ||
+      cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cleanup();
+    return BHMC_ECUDA;
+  }
+  if (hflags[2]) rc = BHMC_ECAPACITY;
+  cleanup();
+  return rc;
+}
+
+// Small device/host scratch shared by the synchronous calls of one context.
+struct IoBlock {
+  DeltaOut delta;
+  int status;
+  int pad;
+  bhmc_mc_stats stats;
+  double energy;
+};
+
+static bhmc_status ctx_alloc(bhmc_ctx* c) {
+  const size_t bytes = arena_bytes(c->S);
+  if (cudaMalloc(&c->arena, bytes) != cudaSuccess) return BHMC_ENOMEM;
+  carve_all(c->S, static_cast<char*>(c->arena));
+  if (cudaMalloc(&c->io, sizeof(IoBlock)) != cudaSuccess) return BHMC_ENOMEM;
+  if (cudaMallocHost(&c->io_host, sizeof(IoBlock)) != cudaSuccess) return BHMC_ENOMEM;
+  return BHMC_OK;
+}
+
+static void ctx_free(bhmc_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->arena);
+  cudaFree(c->io);
+  cudaFreeHost(c->io_host);
+  delete c;
+}
+
+static bhmc_status ctx_make(const bhmc_params* P, int64_t n_mob, int64_t n_fix, const double* q,
+                            const double* xyz, int32_t flags, cudaStream_t stream, bhmc_ctx** out) {
+  bhmc_status rc = validate(P);
+  if (rc != BHMC_OK) return rc;
+  if (n_mob < 0 || n_fix < 0 || n_mob + n_fix < 1 || !q || !xyz || !out) return BHMC_EINVAL;
+  const long long n_tot = n_mob + n_fix + (P->images ? n_mob : 0);
+  if (n_tot >= (1LL << 30)) return BHMC_EINVAL;
+  bhmc_ctx* c = new (std::nothrow) bhmc_ctx();
+  if (!c) return BHMC_ENOMEM;
+  c->P = *P;
+  c->stream = stream;
+  fill_view(c->S, P, n_mob, n_fix);
+  rc = ctx_alloc(c);
+  if (rc == BHMC_OK) rc = build_tree(c, q, xyz, flags);
+  if (rc != BHMC_OK) {
+    ctx_free(c);
+    return rc;
+  }
+  *out = c;
+  return BHMC_OK;
+}
+
+extern "C" {
+
+bhmc_status bhmc_create(const bhmc_params* params, int64_t n_mobile, int64_t n_fixed, const double* q,
+                        const double* xyz, int32_t flags, void* cuda_stream, bhmc_ctx** out) {
+  return ctx_make(params, n_mobile, n_fixed, q, xyz, flags, static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+bhmc_status bhmc_destroy(bhmc_ctx* ctx) {
+  if (!ctx) return BHMC_EINVAL;
+  if (ctx->borrowed) return BHMC_EINVAL;
+  ctx_free(ctx);
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_n_charges(const bhmc_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return BHMC_EINVAL;
+  *n = ctx->S.n_tot;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_get_charges(bhmc_ctx* ctx, double* q, double* xyz, int32_t flags) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  const SysDev& S = ctx->S;
+  if (flags & BHMC_DEVICE_PTRS) {
+    CK(launch_interleave(S, q, xyz, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BHMC_OK;
+  }
+  std::vector<double> buf(4 * (size_t)S.n_tot);
+  CK(cudaMemcpyAsync(buf.data(), S.px, sizeof(double) * S.n_tot, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(buf.data() + S.n_tot, S.py, sizeof(double) * S.n_tot, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(buf.data() + 2 * S.n_tot, S.pz, sizeof(double) * S.n_tot, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(buf.data() + 3 * S.n_tot, S.pq, sizeof(double) * S.n_tot, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int j = 0; j < S.n_tot; ++j) {
+    if (xyz) {
+      xyz[3 * j] = buf[j];
+      xyz[3 * j + 1] = buf[S.n_tot + j];
+      xyz[3 * j + 2] = buf[2 * (size_t)S.n_tot + j];
+    }
+    if (q) q[j] = buf[3 * (size_t)S.n_tot + j];
+  }
+  return BHMC_OK;
+}
+
+static cudaError_t dispatch_delta(bhmc_ctx* c, int i, const double* b, DeltaOut* out) {
+  switch (c->P.p) {
+    case 2: return launch_delta<2>(c->S, c->P.warps, i, b, out, c->stream);
+    case 4: return launch_delta<4>(c->S, c->P.warps, i, b, out, c->stream);
+    default: return launch_delta<6>(c->S, c->P.warps, i, b, out, c->stream);
+  }
+}
+
+bhmc_status bhmc_delta_energy(bhmc_ctx* ctx, int64_t i, const double r_new[3], double* dE,
+                              bhmc_counters* counters) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (i < 0 || i >= ctx->S.n_mob || !r_new || !dE) return BHMC_EINVAL;
+  IoBlock* dio = static_cast<IoBlock*>(ctx->io);
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  CK(cudaMemsetAsync(&dio->delta, 0, sizeof(DeltaOut), ctx->stream));
+  CK(dispatch_delta(ctx, (int)i, r_new, &dio->delta));
+  CK(cudaMemcpyAsync(&hio->delta, &dio->delta, sizeof(DeltaOut), cudaMemcpyDeviceToHost, ctx->stream));
+  rc = sync_err(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (hio->delta.err) return (bhmc_status)hio->delta.err;
+  if (hio->delta.status) return (bhmc_status)hio->delta.status;
+  *dE = hio->delta.dE;
+  if (counters) {
+    counters->visited = hio->delta.cnt[0];
+    counters->accepted = hio->delta.cnt[1];
+    counters->pairs = hio->delta.cnt[2];
+    counters->mac_fp64 = hio->delta.cnt[3];
+  }
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (i < 0 || i >= ctx->S.n_mob || !r_new) return BHMC_EINVAL;
+  IoBlock* dio = static_cast<IoBlock*>(ctx->io);
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  CK(launch_commit(ctx->S, (int)i, r_new, &dio->status, ctx->stream));
+  CK(cudaMemcpyAsync(&hio->status, &dio->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  rc = sync_err(ctx);
+  if (rc != BHMC_OK) return rc;
+  return (bhmc_status)hio->status;
+}
+
+static cudaError_t dispatch_step(bhmc_ctx* c, unsigned long long m, unsigned long long seed, double step,
+                                 MoveRec* rec, bhmc_mc_stats* st) {
+  switch (c->P.p) {
+    case 2: return launch_step<2>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
+    case 4: return launch_step<4>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
+    default: return launch_step<6>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
+  }
+}
+
+bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed, uint64_t move0,
+                         bhmc_mc_stats* stats, bhmc_move_record* records) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!stats || !(step >= 0.0)) return BHMC_EINVAL;
+  IoBlock* dio = static_cast<IoBlock*>(ctx->io);
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  MoveRec* drec = nullptr;
+  if (records && n_moves) {
+    if (cudaMalloc(&drec, sizeof(MoveRec) * n_moves) != cudaSuccess) return BHMC_ENOMEM;
+  }
+  CK(cudaMemsetAsync(&dio->stats, 0, sizeof(bhmc_mc_stats), ctx->stream));
+  for (uint64_t t = 0; t < n_moves; ++t) {
+    if (dispatch_step(ctx, move0 + t, seed, step, drec ? drec + t : nullptr, &dio->stats) != cudaSuccess) {
+      cudaFree(drec);
+      ctx->sticky = BHMC_ECUDA;
+      return BHMC_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(&hio->stats, &dio->stats, sizeof(bhmc_mc_stats), cudaMemcpyDeviceToHost, ctx->stream));
+  if (drec)
+    CK(cudaMemcpyAsync(records, drec, sizeof(MoveRec) * n_moves, cudaMemcpyDeviceToHost, ctx->stream));
+  rc = sync_err(ctx);
+  cudaFree(drec);
+  if (rc != BHMC_OK) return rc;
+  *stats = hio->stats;
+  if (n_moves == 0) bhmc_get_energy(ctx, &stats->energy);
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E) {
+  if (!ctx || !E) return BHMC_EINVAL;
+  CK(cudaMemcpyAsync(E, ctx->S.energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  hio->energy = E;
+  CK(cudaMemcpyAsync(ctx->S.energy, &hio->energy, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BHMC_OK;
+}
+
+static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, int* err) {
+  const int w = 4;
+  switch (c->P.p) {
+    case 2: return launch_energy<2>(c->S, w, grid, partial, err, c->stream);
+    case 4: return launch_energy<4>(c->S, w, grid, partial, err, c->stream);
+    default: return launch_energy<6>(c->S, w, grid, partial, err, c->stream);
+  }
+}
+
+bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!E) return BHMC_EINVAL;
+  const int warps = 4;
+  int grid = (ctx->S.n_tot + warps - 1) / warps;
+  grid = std::min(grid, 152 * 16);
+  double* partial = nullptr;
+  int* derr = nullptr;
+  if (cudaMalloc(&partial, sizeof(double) * grid * warps) != cudaSuccess) return BHMC_ENOMEM;
+  if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cudaFree(partial);
+    return BHMC_ENOMEM;
+  }
+  std::vector<double> h((size_t)grid * warps);
+  int herr = 0;
+  bool ok = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream) == cudaSuccess &&
+            dispatch_energy(ctx, grid, partial, derr) == cudaSuccess &&
+            cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                            ctx->stream) == cudaSuccess &&
+            cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
+            cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  cudaFree(partial);
+  cudaFree(derr);
+  if (!ok) return BHMC_ECUDA;
+  if (herr) return (bhmc_status)herr;
+  double s = 0.0;
+  for (double v : h) s += v;
+  *E = 0.5 * ctx->S.lB * s;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!E) return BHMC_EINVAL;
+  const int nblk = std::max(1, std::min((ctx->S.n_tot + 255) / 256, 152 * 8));
+  double* partial = nullptr;
+  if (cudaMalloc(&partial, sizeof(double) * nblk) != cudaSuccess) return BHMC_ENOMEM;
+  std::vector<double> h(nblk);
+  bool ok = launch_direct_energy(ctx->S, partial, nblk, ctx->stream) == cudaSuccess &&
+            cudaMemcpyAsync(h.data(), partial, sizeof(double) * nblk, cudaMemcpyDeviceToHost, ctx->stream) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  cudaFree(partial);
+  if (!ok) return BHMC_ECUDA;
+  double s = 0.0;
+  for (double v : h) s += v;
+  *E = 0.5 * ctx->S.lB * s;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_export_tree(bhmc_ctx* ctx, int64_t* rows, int64_t max_rows, int64_t* members,
+                             int64_t max_members, double* moments, int64_t* n_rows) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!rows || !members || !n_rows) return BHMC_EINVAL;
+  const SysDev& S = ctx->S;
+  int pool[2];
+  CK(cudaMemcpyAsync(pool, S.pool, sizeof(pool), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t nn = 8 * (size_t)pool[0];
+  const int SC = S.C + 2;
+  std::vector<int4> nb(nn);
+  std::vector<float4> sb(nn * SC);
+  std::vector<double> M;
+  CK(cudaMemcpyAsync(nb.data(), S.nB, sizeof(int4) * nn, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(sb.data(), S.sB, sizeof(float4) * nn * SC, cudaMemcpyDeviceToHost, ctx->stream));
+  if (moments) {
+    M.resize(nn * S.K);
+    CK(cudaMemcpyAsync(M.data(), S.M64, sizeof(double) * nn * S.K, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  int64_t nr = 0, nm = 0;
+  std::vector<int> stack{0};
+  while (!stack.empty()) {
+    const int a = stack.back();
+    stack.pop_back();
+    const int4 b = nb[a];
+    const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
+    if (nr >= max_rows) return BHMC_EINVAL;
+    int depth = 0;
+    for (unsigned long long k = key; k > 1; k >>= 3) ++depth;
+    rows[4 * nr + 0] = depth;
+    rows[4 * nr + 1] = (int64_t)key;
+    rows[4 * nr + 2] = b.x < 0 ? 1 : 0;
+    rows[4 * nr + 3] = b.y;
+    if (moments)
+      for (int t = 0; t < S.K; ++t) moments[nr * S.K + t] = M[(size_t)a * S.K + t];
+    ++nr;
+    if (b.x < 0) {
+      if (nm + b.y > max_members) return BHMC_EINVAL;
+      for (int k = 0; k < b.y; ++k) {
+        const float w = sb[(size_t)a * SC + k].w;
+        int j;
+        std::memcpy(&j, &w, sizeof(int));
+        members[nm + k] = j;
+      }
+      std::sort(members + nm, members + nm + b.y);
+      nm += b.y;
+    } else {
+      for (int o = 7; o >= 0; --o) stack.push_back(b.x + o);
+    }
+  }
+  *n_rows = nr;
+  return BHMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const int64_t* n_mobile,
+                              const int64_t* n_fixed, const double* const* q, const double* const* xyz,
+                              int32_t flags, void* cuda_stream, bhmc_batch** out) {
+  if (n_rep < 1 || !params || !n_mobile || !n_fixed || !q || !xyz || !out) return BHMC_EINVAL;
+  bhmc_status rc = validate(params);
+  if (rc != BHMC_OK) return rc;
+  bhmc_batch* B = new (std::nothrow) bhmc_batch();
+  if (!B) return BHMC_ENOMEM;
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  B->warps = params->warps;
+  B->p = params->p;
+  for (int r = 0; r < n_rep; ++r) {
+    bhmc_ctx* c = nullptr;
+    rc = ctx_make(params, n_mobile[r], n_fixed[r], q[r], xyz[r], flags, B->stream, &c);
+    if (rc != BHMC_OK) {
+      bhmc_batch_destroy(B);
+      return rc;
+    }
+    c->borrowed = true;
+    B->reps.push_back(c);
+  }
+  std::vector<SysDev> views(n_rep);
+  for (int r = 0; r < n_rep; ++r) views[r] = B->reps[r]->S;
+  if (cudaMalloc(&B->d_views, sizeof(SysDev) * n_rep) != cudaSuccess ||
+      cudaMalloc(&B->d_args, sizeof(BatchArgs)) != cudaSuccess ||
+      cudaMallocHost(&B->h_args, sizeof(BatchArgs)) != cudaSuccess ||
+      cudaMalloc(&B->d_seeds, sizeof(unsigned long long) * n_rep) != cudaSuccess ||
+      cudaMalloc(&B->d_next, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&B->d_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess ||
+      cudaMallocHost(&B->h_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess) {
+    bhmc_batch_destroy(B);
+    return BHMC_ENOMEM;
+  }
+  if (cudaMemcpy(B->d_views, views.data(), sizeof(SysDev) * n_rep, cudaMemcpyHostToDevice) != cudaSuccess) {
+    bhmc_batch_destroy(B);
+    return BHMC_ECUDA;
+  }
+  int occ = 0;
+  switch (B->p) {
+    case 2: occ = batch_occupancy<2>(views[0], B->warps); break;
+    case 4: occ = batch_occupancy<4>(views[0], B->warps); break;
+    default: occ = batch_occupancy<6>(views[0], B->warps); break;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  B->grid = std::max(1, std::min(n_rep, std::max(1, occ) * std::max(1, sms)));
+  // Capture {args upload, work counter reset, persistent kernel, stats download}.
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    bhmc_batch_destroy(B);
+    return BHMC_ECUDA;
+  }
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BatchArgs), cudaMemcpyHostToDevice, cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(B->d_next, 0, sizeof(int), cs) == cudaSuccess;
+  cudaError_t le = cudaSuccess;
+  if (ok) {
+    switch (B->p) {
+      case 2: le = launch_batch<2>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
+      case 4: le = launch_batch<4>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
+      default: le = launch_batch<6>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
+    }
+  }
+  ok = ok && le == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(B->h_stats, B->d_stats, sizeof(bhmc_mc_stats) * n_rep, cudaMemcpyDeviceToHost,
+                             cs) == cudaSuccess;
+  const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+  ok = ok && ended && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    bhmc_batch_destroy(B);
+    return BHMC_ECUDA;
+  }
+  *out = B;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_batch_destroy(bhmc_batch* B) {
+  if (!B) return BHMC_EINVAL;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  for (bhmc_ctx* c : B->reps) ctx_free(c);
+  cudaFree(B->d_views);
+  cudaFree(B->d_args);
+  cudaFreeHost(B->h_args);
+  cudaFree(B->d_seeds);
+  cudaFree(B->d_next);
+  cudaFree(B->d_stats);
+  cudaFreeHost(B->h_stats);
+  delete B;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_batch_replica(bhmc_batch* B, int32_t r, bhmc_ctx** ctx) {
+  if (!B || !ctx || r < 0 || r >= (int32_t)B->reps.size()) return BHMC_EINVAL;
+  *ctx = B->reps[r];
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
+                               uint64_t move0, bhmc_mc_stats* stats) {
+  if (!B || !seeds || !(step >= 0.0)) return BHMC_EINVAL;
+  const int n = (int)B->reps.size();
+  for (bhmc_ctx* c : B->reps)
+    if (c->sticky) return BHMC_ESTATE;
+  CK(cudaMemcpyAsync(B->d_seeds, seeds, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  B->h_args->n_moves = n_moves;
+  B->h_args->move0 = move0;
+  B->h_args->step = step;
+  B->h_args->seeds = B->d_seeds;
+  CK(cudaGraphLaunch(B->graph, B->stream));
+  bhmc_status rc = BHMC_OK;
+  for (bhmc_ctx* c : B->reps) {
+    bhmc_status e = sync_err(c);
+    if (e != BHMC_OK && rc == BHMC_OK) rc = e;
+  }
+  if (rc != BHMC_OK) return rc;
+  if (stats) std::memcpy(stats, B->h_stats, sizeof(bhmc_mc_stats) * n);
+  return BHMC_OK;
+}
+
+}  // extern "C"

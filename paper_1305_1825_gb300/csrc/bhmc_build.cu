@@ -1,0 +1,348 @@
+// bhmc_build.cu -- octree construction (Sec. 3.2), the stand-alone local
+// adjustment kernel behind bhmc_commit_move (Sec. 3.3), and direct sums.
+#include "bhmc_build.cuh"
+#include "bhmc_move.cuh"
+
+namespace bhmc {
+
+// Charges from the caller's AoS arrays into the SoA store; images of the
+// mobile ions (position R^2 r/|r|^2, charge alpha q R/|r|) appended.
+__global__ void k_init_charges(SysDev S, const double* q, const double* xyz, int* flags) {
+  const int n_in = S.n_mob + S.n_fix;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_in; j += gridDim.x * blockDim.x) {
+    const double r[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+    S.px[j] = r[0];
+    S.py[j] = r[1];
+    S.pz[j] = r[2];
+    S.pq[j] = q[j];
+    if (j < S.n_mob) {
+      if (!shell_ok(S, r)) atomicMax(&flags[1], 1);
+      if (S.images) {
+        double im[3], qi;
+        const int k = S.n_mob + S.n_fix + j;
+        if (!image_of(S, r, q[j], im, &qi)) {
+          atomicMax(&flags[0], 1);
+          im[0] = im[1] = im[2] = 0.0;
+          qi = 0.0;
+        }
+        S.px[k] = im[0];
+        S.py[k] = im[1];
+        S.pz[k] = im[2];
+        S.pq[k] = qi;
+      }
+    }
+  }
+}
+
+__global__ void k_keys(SysDev S, int* perm, int* flags) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.x * blockDim.x) {
+    const unsigned long long k = point_key(S, S.px[j], S.py[j], S.pz[j]);
+    if (k == 0ULL) atomicMax(&flags[0], 1);
+    S.ckey[j] = k;
+    perm[j] = j;
+  }
+}
+
+__global__ void k_init_root(SysDev S, int* seg) {
+  if (threadIdx.x < 8) {
+    const int o = threadIdx.x;
+    const float h = (float)(0.5 * S.root_side);
+    const float c[3] = {(float)(S.root_lo[0] + 0.5 * S.root_side), (float)(S.root_lo[1] + 0.5 * S.root_side),
+                        (float)(S.root_lo[2] + 0.5 * S.root_side)};
+    S.nA[o] = o == 0 ? make_float4(c[0], c[1], c[2], h) : make_float4(0.f, 0.f, 0.f, 0.f);
+    S.nB[o] = make_int4(-1, o == 0 ? S.n_tot : 0, o == 0 ? 1 : 0, 0);
+    seg[o] = 0;
+  }
+  if (threadIdx.x == 0) {
+    S.pool[0] = 1;
+    S.pool[1] = 0;
+    *S.energy = 0.0;
+    *S.err = 0;
+  }
+}
+
+// Split every cluster of `list` (one block each) into its eight octants: a
+// stable partition of its segment of `perm` by the octant digit of the charge
+// keys at depth+1; children get group base_group + blockIdx.x.
+__global__ void __launch_bounds__(256) k_split_level(SysDev S, const int* list, int base_group, int depth,
+                                                     int* perm, int* perm2, int* seg, int* next_flags) {
+  __shared__ int counts[8], start[8], run[8], wtot[8][8];
+  const int node = list[blockIdx.x];
+  const int c0 = 8 * (base_group + blockIdx.x);
+  const int st = seg[node];
+  const int4 nb = S.nB[node];
+  const int cnt = nb.y;
+  const int sh = 3 * (S.Dmax - depth - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 8) counts[threadIdx.x] = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+    atomicAdd(&counts[(int)((S.ckey[perm[st + k]] >> sh) & 7ULL)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int o = 0; o < 8; ++o) {
+      start[o] = s;
+      run[o] = s;
+      s += counts[o];
+    }
+  }
+  __syncthreads();
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const bool valid = k < cnt;
+    const int e = valid ? perm[st + k] : 0;
+    const int o = valid ? (int)((S.ckey[e] >> sh) & 7ULL) : 8;
+    int rank = 0;
+    for (int d = 0; d < 8; ++d) {
+      const unsigned m = __ballot_sync(0xffffffffu, o == d);
+      if (o == d) rank = __popc(m & ((1u << lane) - 1u));
+      if (lane == 0) wtot[warp][d] = __popc(m);
+    }
+    __syncthreads();
+    if (valid) {
+      int off = run[o];
+      for (int w = 0; w < warp; ++w) off += wtot[w][o];
+      perm2[st + off + rank] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      int add = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) add += wtot[w][threadIdx.x];
+      run[threadIdx.x] += add;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) perm[st + k] = perm2[st + k];
+  if (threadIdx.x < 8) {
+    const int o = threadIdx.x;
+    const float4 a = S.nA[node];
+    const float hc = 0.5f * a.w;
+    const unsigned long long key = ((unsigned long long)(unsigned)nb.w << 32) | (unsigned)nb.z;
+    const unsigned long long ck = (key << 3) | (unsigned long long)o;
+    S.nA[c0 + o] = make_float4((o & 1) ? a.x + hc : a.x - hc, (o & 2) ? a.y + hc : a.y - hc,
+                               (o & 4) ? a.z + hc : a.z - hc, hc);
+    S.nB[c0 + o] = make_int4(-1, counts[o], (int)(unsigned)(ck & 0xffffffffULL), (int)(unsigned)(ck >> 32));
+    seg[c0 + o] = st + start[o];
+    next_flags[8 * blockIdx.x + o] = (counts[o] > S.C && depth + 1 < S.Dmax) ? c0 + o : -1;
+  }
+  if (threadIdx.x == 0) S.nB[node].x = c0;
+}
+
+// Order-preserving compaction of the non-negative entries (one block).
+__global__ void __launch_bounds__(1024) k_compact(const int* in, int n, int* out, int* n_out) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int v = k < n ? in[k] : -1;
+    const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int off = carry;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (v >= 0) out[off + __popc(m & ((1u << lane) - 1u))] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+      carry += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_out = carry;
+}
+
+// Leaves receive their slots (charge positions as float pairs, charge, index).
+__global__ void k_fill_leaves(SysDev S, int n_nodes, const int* perm, const int* seg, int* flags) {
+  const int SC = S.C + 2;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < n_nodes; nd += gridDim.x * blockDim.x) {
+    const int4 b = S.nB[nd];
+    if (b.z == 0 && b.w == 0) continue;  // empty slot of the root group
+    if (b.x >= 0) continue;
+    if (b.y > S.C) {
+      atomicMax(&flags[2], 1);
+      continue;
+    }
+    for (int k = 0; k < b.y; ++k) {
+      const int j = perm[seg[nd] + k];
+      const float2 fx = split2(S.px[j]), fy = split2(S.py[j]), fz = split2(S.pz[j]);
+      S.sA[nd * SC + k] = make_float4(fx.x, fy.x, fz.x, (float)S.pq[j]);
+      S.sB[nd * SC + k] = make_float4(fx.y, fy.y, fz.y, __int_as_float(j));
+      S.leaf_of[j] = nd;
+      S.slot_of[j] = k;
+    }
+  }
+}
+
+// M_A^n = sum_{j in A} q_j (r_j - r_A)^n in FP64.  Small clusters: one thread
+// per (cluster, term), members in index order.  Large clusters: one block per
+// cluster and term-by-term block reductions.
+__global__ void k_moments_small(SysDev S, int n_nodes, const int* perm, const int* seg, int big) {
+  const long long total = (long long)n_nodes * S.K;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int nd = (int)(it / S.K), t = (int)(it - (long long)nd * S.K);
+    const int4 b = S.nB[nd];
+    if (b.z == 0 && b.w == 0) continue;
+    if (b.y > big) continue;
+    const float4 c = S.nA[nd];
+    int n1, n2, n3;
+    term_exponents(t, n1, n2, n3);
+    double M = 0.0;
+    for (int k = 0; k < b.y; ++k) {
+      const int j = perm[seg[nd] + k];
+      M = __dadd_rn(M, mono_term(n1, n2, n3, S.pq[j], __dsub_rn(S.px[j], (double)c.x),
+                                 __dsub_rn(S.py[j], (double)c.y), __dsub_rn(S.pz[j], (double)c.z)));
+    }
+    S.M64[(size_t)nd * S.K + t] = M;
+    if (S.prec == BHMC_PREC_F32) S.M32[m32_index(S, nd, t)] = __double2float_rn(M);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_moments_big(SysDev S, int n_nodes, const int* perm, const int* seg,
+                                                     int big) {
+  __shared__ double red[8];
+  for (int nd = blockIdx.x; nd < n_nodes; nd += gridDim.x) {
+    const int4 b = S.nB[nd];
+    if ((b.z == 0 && b.w == 0) || b.y <= big) continue;
+    const float4 c = S.nA[nd];
+    for (int t = 0; t < S.K; ++t) {
+      int n1, n2, n3;
+      term_exponents(t, n1, n2, n3);
+      double M = 0.0;
+      for (int k = threadIdx.x; k < b.y; k += blockDim.x) {
+        const int j = perm[seg[nd] + k];
+        M += mono_term(n1, n2, n3, S.pq[j], __dsub_rn(S.px[j], (double)c.x), __dsub_rn(S.py[j], (double)c.y),
+                       __dsub_rn(S.pz[j], (double)c.z));
+      }
+      for (int o = 16; o > 0; o >>= 1) M += __shfl_xor_sync(0xffffffffu, M, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = M;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        S.M64[(size_t)nd * S.K + t] = s;
+        if (S.prec == BHMC_PREC_F32) S.M32[m32_index(S, nd, t)] = __double2float_rn(s);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Stand-alone local adjustment (bhmc_commit_move): paths by descent from the root.
+__global__ void __launch_bounds__(128) k_commit(SysDev S, int i, double bx, double by, double bz, int* status) {
+  __shared__ MoveSh sh;
+  if (threadIdx.x == 0) {
+    const double b[3] = {bx, by, bz};
+    const int o = setup_move(S, sh, i, b);
+    sh.go = o < 0;
+    *status = o < 0 ? 0 : (o == BHMC_REJECT_DOMAIN ? BHMC_EDOMAIN : BHMC_EOVERLAP);
+  }
+  for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
+  __syncthreads();
+  if (!sh.go) return;
+  complete_paths(S, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sh.go = !capacity_violation(S, sh);
+    if (!sh.go) *status = BHMC_ECAPACITY;
+  }
+  __syncthreads();
+  if (!sh.go) return;
+  commit_move_block(S, sh);
+}
+
+// Direct O(N^2) energy, FP64: partial[block] = sum over its rows i of
+// q_i sum_{j != i} q_j / r_ij.
+__global__ void __launch_bounds__(256) k_direct_energy(const double* px, const double* py, const double* pz,
+                                                       const double* pq, int n, double* partial) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double xi = px[i], yi = py[i], zi = pz[i];
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const double dx = px[j] - xi, dy = py[j] - yi, dz = pz[j] - zi;
+      s += pq[j] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    acc += pq[i] * s;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_interleave(SysDev S, double* q, double* xyz) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.x * blockDim.x) {
+    if (q) q[j] = S.pq[j];
+    if (xyz) {
+      xyz[3 * j] = S.px[j];
+      xyz[3 * j + 1] = S.py[j];
+      xyz[3 * j + 2] = S.pz[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+static inline int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+cudaError_t build_init_charges(const SysDev& S, const double* q, const double* xyz, int* flags,
+                               cudaStream_t st) {
+  k_init_charges<<<grid_for(S.n_mob + S.n_fix, 256), 256, 0, st>>>(S, q, xyz, flags);
+  return cudaGetLastError();
+}
+cudaError_t build_keys(const SysDev& S, int* perm, int* flags, cudaStream_t st) {
+  k_keys<<<grid_for(S.n_tot, 256), 256, 0, st>>>(S, perm, flags);
+  return cudaGetLastError();
+}
+cudaError_t build_root(const SysDev& S, int* seg, cudaStream_t st) {
+  k_init_root<<<1, 32, 0, st>>>(S, seg);
+  return cudaGetLastError();
+}
+cudaError_t build_split_level(const SysDev& S, const int* list, int n_list, int base_group, int depth,
+                              int* perm, int* perm2, int* seg, int* next_flags, cudaStream_t st) {
+  k_split_level<<<n_list, 256, 0, st>>>(S, list, base_group, depth, perm, perm2, seg, next_flags);
+  return cudaGetLastError();
+}
+cudaError_t build_compact(const int* in, int n, int* out, int* n_out, cudaStream_t st) {
+  k_compact<<<1, 1024, 0, st>>>(in, n, out, n_out);
+  return cudaGetLastError();
+}
+cudaError_t build_leaves_moments(const SysDev& S, int n_nodes, const int* perm, const int* seg, int* flags,
+                                 cudaStream_t st) {
+  k_fill_leaves<<<grid_for(n_nodes, 256), 256, 0, st>>>(S, n_nodes, perm, seg, flags);
+  const int big = 64;
+  k_moments_small<<<grid_for((long long)n_nodes * S.K, 256), 256, 0, st>>>(S, n_nodes, perm, seg, big);
+  k_moments_big<<<n_nodes < 4096 ? n_nodes : 4096, 256, 0, st>>>(S, n_nodes, perm, seg, big);
+  return cudaGetLastError();
+}
+cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st) {
+  k_commit<<<1, 128, 0, st>>>(S, i, b[0], b[1], b[2], status);
+  return cudaGetLastError();
+}
+cudaError_t launch_direct_energy(const SysDev& S, double* partial, int nblk, cudaStream_t st) {
+  k_direct_energy<<<nblk, 256, 0, st>>>(S.px, S.py, S.pz, S.pq, S.n_tot, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_interleave(const SysDev& S, double* q, double* xyz, cudaStream_t st) {
+  k_interleave<<<grid_for(S.n_tot, 256), 256, 0, st>>>(S, q, xyz);
+  return cudaGetLastError();
+}
+
+}  // namespace bhmc

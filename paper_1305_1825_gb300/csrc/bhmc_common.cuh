@@ -1,0 +1,174 @@
+// bhmc_common.cuh -- device-side data layout and helpers of the GB300 treecode
+// Monte Carlo (Gan & Xu 2013).  Everything here is written for sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bhmc.h"
+
+#define BHMC_MAX_P 6
+#define BHMC_MAX_D 20
+#define BHMC_MAX_WARPS 4
+#define BHMC_STACK 768          // traversal stack entries per warp
+#define BHMC_MAX_C 32
+
+namespace bhmc {
+
+__host__ __device__ constexpr int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+__host__ __device__ constexpr int pad4(int k) { return (k + 3) & ~3; }
+// graded order of multi-indices (k = 0..p; n1 = k..0; n2 = k-n1..0), Eq. (3.3)
+__host__ __device__ constexpr int tidx(int n1, int n2, int n3) {
+  return (n1 + n2 + n3) * (n1 + n2 + n3 + 1) * (n1 + n2 + n3 + 2) / 6 +
+         (n2 + n3) * (n2 + n3 + 1) / 2 + n3;
+}
+
+// Device view of one system.  Node storage: 8 contiguous children per group;
+// group 0 holds the root at node 0 (nodes 1..7 stay empty).  Per node:
+//   nA = {cx, cy, cz, h} (centre and half side, exact dyadic floats),
+//   nB = {first_child or -1, count, key_lo, key_hi} (Morton key with a leading 1).
+// Leaf slots: node*C + k, sA = {x_hi, y_hi, z_hi, q}, sB = {x_lo, y_lo, z_lo, idx}
+// where x = x_hi + x_lo is the FP64 position split into two floats.
+struct SysDev {
+  int n_mob, n_fix, n_tot;
+  int p, K, Kp, N0, C, Dmax;
+  int images, shell, prec, layout;
+  double lB, beta, theta2;
+  float theta2f, lBf;
+  double root_lo[3], root_side;
+  double inv_hmin;          // 2^Dmax / side (a power of two)
+  long long root_cell[3];   // root_lo * inv_hmin (integers)
+  double rmin, rmax;        // shell radii
+  double img_R, img_alpha;
+  // charges
+  double *px, *py, *pz, *pq;
+  unsigned long long* ckey;
+  int* leaf_of;
+  int* slot_of;
+  // nodes
+  int node_cap, group_cap;
+  float4* nA;
+  int4* nB;
+  float* M32;   // SoA [K][node_cap] or AoS [node_cap][Kp]
+  double* M64;  // [node_cap][K]
+  float4* sA;
+  float4* sB;
+  int* pool;    // pool[0] = next unused group, pool[1] = number of free groups
+  int* free_list;
+  // state
+  double* energy;
+  int* err;
+};
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// --------------------------------------------------------------------------
+// Exact depth-Dmax cell index: x * 2^Dmax / side is a power-of-two scaling
+// (exact), floor is exact, so the cell equals the one reached by comparing x
+// with every cluster mid-plane (ties to the upper half).
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+
+// Returns 0 if the point is outside the root cube.
+__device__ __forceinline__ unsigned long long point_key(const SysDev& S, double x, double y,
+                                                        double z) {
+  long long lim = 1LL << S.Dmax;
+  long long kx = (long long)floor(__dmul_rn(x, S.inv_hmin)) - S.root_cell[0];
+  long long ky = (long long)floor(__dmul_rn(y, S.inv_hmin)) - S.root_cell[1];
+  long long kz = (long long)floor(__dmul_rn(z, S.inv_hmin)) - S.root_cell[2];
+  if (kx < 0 || ky < 0 || kz < 0 || kx >= lim || ky >= lim || kz >= lim) return 0ULL;
+  return (1ULL << (3 * S.Dmax)) | spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+}
+
+__device__ __forceinline__ int key_depth(unsigned long long k) { return (63 - __clzll(k)) / 3; }
+
+// x = hi + lo with hi = round(x), lo = round(x - hi)
+__device__ __forceinline__ float2 split2(double x) {
+  float hi = __double2float_rn(x);
+  float lo = __double2float_rn(__dsub_rn(x, (double)hi));
+  return make_float2(hi, lo);
+}
+
+// Image of a charge q at r (FP64, same operation order as the definition:
+// r2 = (x*x + y*y) + z*z, f = R*R / r2, image = f r, charge = ((alpha q) R) / |r|).
+__device__ __forceinline__ bool image_of(const SysDev& S, const double r[3], double q,
+                                         double out[3], double* qim) {
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])),
+                        __dmul_rn(r[2], r[2]));
+  if (!(r2 > 0.0)) return false;
+  double rn = __dsqrt_rn(r2);
+  double f = __ddiv_rn(__dmul_rn(S.img_R, S.img_R), r2);
+  out[0] = __dmul_rn(f, r[0]);
+  out[1] = __dmul_rn(f, r[1]);
+  out[2] = __dmul_rn(f, r[2]);
+  *qim = __ddiv_rn(__dmul_rn(__dmul_rn(S.img_alpha, q), S.img_R), rn);
+  return true;
+}
+
+__device__ __forceinline__ bool in_root(const SysDev& S, const double x[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double hi = __dadd_rn(S.root_lo[a], S.root_side);
+    if (!(x[a] >= S.root_lo[a]) || !(x[a] < hi)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool shell_ok(const SysDev& S, const double x[3]) {
+  if (!S.shell) return true;
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])),
+                        __dmul_rn(x[2], x[2]));
+  return r2 >= __dmul_rn(S.rmin, S.rmin) && r2 <= __dmul_rn(S.rmax, S.rmax);
+}
+
+__device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S.err, 0, code); }
+
+// Moment term t (graded order) of charge q at offset d, in FP64 with the
+// monomial built by repeated multiplication: q * ((dx^n1 * dy^n2) * dz^n3).
+__device__ __forceinline__ void term_exponents(int t, int& n1, int& n2, int& n3) {
+  int k = 0;
+  while (nterms(k) <= t) ++k;
+  int r = t - (k > 0 ? nterms(k - 1) : 0);
+  int a = 0;  // a = k - n1: block of size a+1
+  while ((a + 1) * (a + 2) / 2 <= r) ++a;
+  int w = r - a * (a + 1) / 2;  // = a - n2
+  n1 = k - a;
+  n2 = a - w;
+  n3 = k - n1 - n2;
+}
+
+__device__ __forceinline__ double mono_term(int n1, int n2, int n3, double q, double dx, double dy,
+                                            double dz) {
+  double px = 1.0, py = 1.0, pz = 1.0;
+  for (int k = 0; k < n1; ++k) px = __dmul_rn(px, dx);
+  for (int k = 0; k < n2; ++k) py = __dmul_rn(py, dy);
+  for (int k = 0; k < n3; ++k) pz = __dmul_rn(pz, dz);
+  return __dmul_rn(q, __dmul_rn(__dmul_rn(px, py), pz));
+}
+
+__device__ __forceinline__ int m32_index(const SysDev& S, int node, int t) {
+  return S.layout == BHMC_LAYOUT_SOA ? t * S.node_cap + node : node * S.Kp + t;
+}
+
+}  // namespace bhmc

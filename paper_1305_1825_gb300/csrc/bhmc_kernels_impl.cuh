@@ -1,0 +1,74 @@
+// bhmc_kernels_impl.cuh -- definitions of the per-order launchers; included by
+// one translation unit per multipole order with BHMC_P defined.
+#pragma once
+
+#include "bhmc_launch.cuh"
+#include "bhmc_move.cuh"
+
+namespace bhmc {
+
+
+template <>
+cudaError_t launch_delta<BHMC_P>(const SysDev& S, int warps, int i, const double* b, DeltaOut* out,
+                                 cudaStream_t st) {
+  if (S.prec == BHMC_PREC_F64)
+    k_delta<BHMC_P, double, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, i, b[0], b[1], b[2], out);
+  else if (S.layout == BHMC_LAYOUT_AOS)
+    k_delta<BHMC_P, float, BHMC_LAYOUT_AOS><<<1, 32 * warps, 0, st>>>(S, i, b[0], b[1], b[2], out);
+  else
+    k_delta<BHMC_P, float, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, i, b[0], b[1], b[2], out);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_step<BHMC_P>(const SysDev& S, int warps, unsigned long long m, unsigned replica,
+                                unsigned long long seed, double step, MoveRec* rec,
+                                bhmc_mc_stats* stats, cudaStream_t st) {
+  const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+  if (S.prec == BHMC_PREC_F64)
+    k_step<BHMC_P, double, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, m, replica, key, step, rec, stats);
+  else if (S.layout == BHMC_LAYOUT_AOS)
+    k_step<BHMC_P, float, BHMC_LAYOUT_AOS><<<1, 32 * warps, 0, st>>>(S, m, replica, key, step, rec, stats);
+  else
+    k_step<BHMC_P, float, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, m, replica, key, step, rec, stats);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_batch<BHMC_P>(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
+                                 const BatchArgs* args, int* next, bhmc_mc_stats* stats,
+                                 cudaStream_t st) {
+  if (S0.prec == BHMC_PREC_F64)
+    k_batch<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+  else if (S0.layout == BHMC_LAYOUT_AOS)
+    k_batch<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+  else
+    k_batch<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+  return cudaGetLastError();
+}
+
+template <>
+int batch_occupancy<BHMC_P>(const SysDev& S0, int warps) {
+  int n = 0;
+  if (S0.prec == BHMC_PREC_F64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<BHMC_P, double, BHMC_LAYOUT_SOA>, 32 * warps, 0);
+  else if (S0.layout == BHMC_LAYOUT_AOS)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<BHMC_P, float, BHMC_LAYOUT_AOS>, 32 * warps, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<BHMC_P, float, BHMC_LAYOUT_SOA>, 32 * warps, 0);
+  return n;
+}
+
+template <>
+cudaError_t launch_energy<BHMC_P>(const SysDev& S, int warps, int grid, double* partial, int* err,
+                                  cudaStream_t st) {
+  if (S.prec == BHMC_PREC_F64)
+    k_energy<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+  else if (S.layout == BHMC_LAYOUT_AOS)
+    k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+  else
+    k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+  return cudaGetLastError();
+}
+
+}  // namespace bhmc

@@ -1,0 +1,45 @@
+// bhmc_launch.cuh -- host launchers of the kernels that are instantiated per
+// multipole order p (one translation unit per p so they compile in parallel).
+#pragma once
+
+#include "bhmc_common.cuh"
+
+namespace bhmc {
+
+struct DeltaOut;
+struct MoveRec;
+struct BatchArgs;
+
+template <int P>
+cudaError_t launch_delta(const SysDev& S, int warps, int i, const double* b, DeltaOut* out,
+                         cudaStream_t st);
+template <int P>
+cudaError_t launch_step(const SysDev& S, int warps, unsigned long long m, unsigned replica,
+                        unsigned long long seed, double step, MoveRec* rec, bhmc_mc_stats* stats,
+                        cudaStream_t st);
+template <int P>
+cudaError_t launch_batch(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
+                         const BatchArgs* args, int* next, bhmc_mc_stats* stats, cudaStream_t st);
+template <int P>
+int batch_occupancy(const SysDev& S0, int warps);
+template <int P>
+cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial, int* err,
+                          cudaStream_t st);
+
+#define BHMC_EXTERN_P(P)                                                                         \
+  template <> cudaError_t launch_delta<P>(const SysDev&, int, int, const double*, DeltaOut*, \
+                                              cudaStream_t);                                     \
+  template <> cudaError_t launch_step<P>(const SysDev&, int, unsigned long long, unsigned,   \
+                                             unsigned long long, double, MoveRec*,               \
+                                             bhmc_mc_stats*, cudaStream_t);                      \
+  template <> cudaError_t launch_batch<P>(const SysDev&, int, const SysDev*, int, int,       \
+                                              const BatchArgs*, int*, bhmc_mc_stats*,            \
+                                              cudaStream_t);                                     \
+  template <> int batch_occupancy<P>(const SysDev&, int);                                    \
+  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, int*, cudaStream_t);
+
+BHMC_EXTERN_P(2)
+BHMC_EXTERN_P(4)
+BHMC_EXTERN_P(6)
+
+}  // namespace bhmc
