@@ -4,9 +4,11 @@ Bars:
   * tree structure, leaf membership, interaction-list counters, proposals and
     accept/reject sequences: exact (decisions with |beta dE + ln alpha| < 1e-6
     are flagged and may differ);
-  * dE, FP32 traversal: |dE_gpu - dE_oracle| <= 1e-5 |dE_oracle| + 1e-6 * A, where
-    A = l_B sum over the interaction lists of |term| (the FP32 conditioning of
-    the sum: every term carries a relative rounding error of a few 2^-24);
+  * dE, FP32 traversal: |dE_gpu - dE_oracle| <= 1e-5 |dE_oracle| + 5e-7 * A, where
+    A = l_B sum over the interaction lists of |term|: each FP32 term (float-pair
+    difference, r^2, rsqrt, charge and weight products) carries a relative
+    error of at most about 8 * 2^-24 = 4.8e-7, so 5e-7 * A bounds the sum of
+    the per-term errors; the relative bar alone is unattainable when dE -> 0;
   * dE, FP64 mode: |dE_gpu - dE_oracle| <= 1e-12 * A.
 """
 import numpy as np
@@ -16,7 +18,7 @@ from paper_1305_1825_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL, FLOOR32, FLOOR64 = 1e-5, 1e-6, 1e-12
+REL, FLOOR32, FLOOR64 = 1e-5, 5e-7, 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -209,4 +211,5 @@ def test_full_energy(bh, oracle_mod):
             e_ref = ref.energy_tree()
             scale = float(np.abs(wl["q"]).sum())
             assert abs(e_tree - e_ref) <= tol * abs(e_ref) + tol * scale
-            assert ctx.energy_direct() == pytest.approx(ref.energy_direct(), rel=1e-11)
+            # FP64 sums of N^2/2 mixed-sign pairs in different orders
+            assert ctx.energy_direct() == pytest.approx(ref.energy_direct(), rel=1e-9)
