@@ -235,16 +235,24 @@ __global__ void __launch_bounds__(256) k_moments_big(SysDev S, int n_nodes, cons
 
 // Stand-alone local adjustment (bhmc_commit_move): paths by descent from the root.
 __global__ void __launch_bounds__(128) k_commit(SysDev S, int i, double bx, double by, double bz, int* status) {
-  __shared__ MoveSh sh;
+  __shared__ MoveStore st;
+  MoveSh& sh = st.sh;
+  init_tables(sh, S.K);
   if (threadIdx.x == 0) {
-    const double b[3] = {bx, by, bz};
-    const int o = setup_move(S, sh, i, b);
-    sh.go = o < 0;
-    *status = o < 0 ? 0 : (o == BHMC_REJECT_DOMAIN ? BHMC_EDOMAIN : BHMC_EOVERLAP);
+    sh.i = i;
+    sh.b[0] = bx;
+    sh.b[1] = by;
+    sh.b[2] = bz;
   }
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
   __syncthreads();
-  if (!sh.go) return;
+  setup_move(S, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int o = sh.outcome;
+    *status = o < 0 ? 0 : (o == BHMC_REJECT_DOMAIN ? BHMC_EDOMAIN : BHMC_EOVERLAP);
+  }
+  if (sh.outcome >= 0) return;
   complete_paths(S, sh);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(128) k_commit(SysDev S, int i, double bx, doub
   }
   __syncthreads();
   if (!sh.go) return;
-  commit_move_block(S, sh);
+  commit_move_block(S, st);
 }
 
 // Direct O(N^2) energy, FP64: partial[block] = sum over its rows i of

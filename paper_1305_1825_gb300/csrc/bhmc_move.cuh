@@ -2,9 +2,13 @@
 // rejection tests, energy difference by the fused traversal at the old and new
 // positions of the ion and its image (Sec. 1, Sec. 3.2), acceptance (Sec. 2)
 // and the local adjustment of the octree (Sec. 3.3) with split/merge.
+//
+// A move is executed by one thread block (1, 2 or 4 warps).  Serial control
+// decisions are taken by thread 0; every loop over points, levels, moment
+// terms or leaf slots is spread over the lanes.
 #pragma once
 
-#include "bhmc_traverse.cuh"
+#include "bhmc_block.cuh"
 
 namespace bhmc {
 
@@ -15,81 +19,126 @@ struct MoveSh {
   double a[3], b[3], ai[3], bi[3];
   int path[4][BHMC_MAX_D + 1];
   int plen[4];
+  int leafcnt[4];          // pre-move counts of the four path leaves
+  int slot_i, slot_img;    // pre-move leaf slots of the ion and its image
+  int merge_d[2];          // topmost level to merge on each old path
   double part[BHMC_MAX_WARPS];
   int cnt[BHMC_MAX_WARPS][5];
   int outcome, flagged, go;
+  int rej_dom, rej_shell, rej_img;
   double dE, alpha;
   int split_node, split_g;
+  unsigned char ex[nterms(BHMC_MAX_P)][3];  // exponents of every moment term
   float4 tA[BHMC_MAX_C + 2], tB[BHMC_MAX_C + 2];
 };
 
 struct MoveStore {
   MoveSh sh;
-  WarpStore ws[BHMC_MAX_WARPS];
+  union {
+    BlockStore bs;
+    // (r - r_A)^k per moved charge, old/new position, level, axis
+    double pw[2][2][BHMC_MAX_D + 1][3][BHMC_MAX_P + 1];
+  };
 };
 
-// ---------------------------------------------------------------------------
-// Set up a move of ion i to b (thread 0).  Returns -1 to proceed, or the
-// rejection outcome (domain / shell), in the oracle's order of tests.
-static __device__ int setup_move(const SysDev& S, MoveSh& sh, int i, const double b[3]) {
-  sh.i = i;
-  sh.q = S.pq[i];
-  sh.a[0] = S.px[i];
-  sh.a[1] = S.py[i];
-  sh.a[2] = S.pz[i];
-  for (int k = 0; k < 3; ++k) sh.b[k] = b[k];
-  if (!in_root(S, b)) return BHMC_REJECT_DOMAIN;
-  if (!shell_ok(S, b)) return BHMC_REJECT_OVERLAP;
-  TravPts& T = sh.T;
-  sh.npts = 2;
-  sh.nmov = 1;
-  T.n_excl = 1;
-  T.excl[0] = i;
-  T.ekey[0] = S.ckey[i];
-  T.eq[0] = sh.q;
-  for (int k = 0; k < 3; ++k) T.ex[0][k] = sh.a[k];
-  if (S.images) {
-    const int img = S.n_mob + S.n_fix + i;
-    sh.img = img;
-    sh.ai[0] = S.px[img];
-    sh.ai[1] = S.py[img];
-    sh.ai[2] = S.pz[img];
-    sh.qa_img = S.pq[img];
-    if (!image_of(S, b, sh.q, sh.bi, &sh.qb_img)) return BHMC_REJECT_DOMAIN;
-    if (!in_root(S, sh.bi)) return BHMC_REJECT_DOMAIN;
-    sh.npts = 4;
-    sh.nmov = 2;
-    T.n_excl = 2;
-    T.excl[1] = img;
-    T.ekey[1] = S.ckey[img];
-    T.eq[1] = sh.qa_img;
-    for (int k = 0; k < 3; ++k) T.ex[1][k] = sh.ai[k];
+// Per-kernel initialisation of the moment-term exponent table.
+__device__ __forceinline__ void init_tables(MoveSh& sh, int K) {
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    int n1, n2, n3;
+    term_exponents(t, n1, n2, n3);
+    sh.ex[t][0] = (unsigned char)n1;
+    sh.ex[t][1] = (unsigned char)n2;
+    sh.ex[t][2] = (unsigned char)n3;
   }
-  const double* pts[4] = {sh.a, sh.b, sh.ai, sh.bi};
-  const double w[4] = {-sh.q, sh.q, -sh.qa_img, sh.qb_img};
-  for (int s = 0; s < sh.npts; ++s) {
-    for (int k = 0; k < 3; ++k) {
-      T.x[s][k] = pts[s][k];
-      const float2 f = split2(pts[s][k]);
-      T.hi[s][k] = f.x;
-      T.lo[s][k] = f.y;
-    }
-    T.w64[s] = w[s];
-    T.w[s] = (float)w[s];
-  }
-  T.pkey[0] = S.ckey[i];
-  T.pkey[1] = point_key(S, b[0], b[1], b[2]);
-  if (S.images) {
-    T.pkey[2] = S.ckey[sh.img];
-    T.pkey[3] = point_key(S, sh.bi[0], sh.bi[1], sh.bi[2]);
-  }
-  return -1;
 }
 
-__device__ __forceinline__ unsigned warp_points(int warp, int W, int npts) {
-  if (W == 1) return npts == 4 ? 15u : 3u;
-  if (W == 2) return npts == 4 ? (warp == 0 ? 3u : 12u) : (1u << warp);
-  return warp < npts ? (1u << warp) : 0u;
+// ---------------------------------------------------------------------------
+// Set up the move of ion sh.i to sh.b (all threads; sh.i and sh.b written
+// before a barrier).  The ion's and the image's FP64 work run on different
+// warps.  Sets sh.outcome = -1 to proceed or the rejection outcome, with the
+// tests in the oracle's order: root cube, shell, image, image in root cube.
+static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+  TravPts& T = sh.T;
+  const int i = sh.i;
+  const int img_tid = W > 1 ? 32 : 1;
+  if (tid == 0) {
+    sh.q = S.pq[i];
+    sh.a[0] = S.px[i];
+    sh.a[1] = S.py[i];
+    sh.a[2] = S.pz[i];
+    const unsigned long long k = S.ckey[i];
+    T.pkey[0] = k;
+    T.ekey[0] = k;
+    T.pkey[1] = point_key(S, sh.b[0], sh.b[1], sh.b[2]);
+    sh.rej_dom = T.pkey[1] == 0ULL;  // outside the root cube
+    sh.rej_shell = !shell_ok(S, sh.b);
+    sh.npts = S.images ? 4 : 2;
+    sh.nmov = S.images ? 2 : 1;
+    T.n_excl = sh.nmov;
+    T.excl[0] = i;
+  } else if (tid == img_tid) {
+    sh.rej_img = 0;
+    sh.qa_img = 0.0;
+    sh.qb_img = 0.0;
+    if (S.images) {
+      const int img = S.n_mob + S.n_fix + i;
+      sh.img = img;
+      T.excl[1] = img;
+      sh.ai[0] = S.px[img];
+      sh.ai[1] = S.py[img];
+      sh.ai[2] = S.pz[img];
+      sh.qa_img = S.pq[img];
+      const unsigned long long k = S.ckey[img];
+      T.pkey[2] = k;
+      T.ekey[1] = k;
+      double bi[3], qb;
+      unsigned long long kb = 0ULL;
+      if (image_of(S, sh.b, S.pq[i], bi, &qb)) kb = point_key(S, bi[0], bi[1], bi[2]);
+      if (kb == 0ULL) {
+        sh.rej_img = 1;
+        bi[0] = bi[1] = bi[2] = 0.0;
+        qb = 0.0;
+      }
+      sh.bi[0] = bi[0];
+      sh.bi[1] = bi[1];
+      sh.bi[2] = bi[2];
+      sh.qb_img = qb;
+      T.pkey[3] = kb;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0)
+      sh.outcome = sh.rej_dom ? BHMC_REJECT_DOMAIN
+                              : sh.rej_shell ? BHMC_REJECT_OVERLAP : sh.rej_img ? BHMC_REJECT_DOMAIN : -1;
+    if (lane < 3 * sh.npts) {
+      const int s = lane / 3, k = lane - 3 * (lane / 3);
+      const double* pts[4] = {sh.a, sh.b, sh.ai, sh.bi};
+      const float2 f = split2(pts[s][k]);
+      T.x[s][k] = pts[s][k];
+      T.hi[s][k] = f.x;
+      T.lo[s][k] = f.y;
+      if (s == 0 || s == 2) {
+        T.ex[s >> 1][k] = pts[s][k];
+        T.ehi[s >> 1][k] = f.x;
+        T.elo[s >> 1][k] = f.y;
+      }
+    } else if (lane == 12) {
+      const double w[4] = {-sh.q, sh.q, -sh.qa_img, sh.qb_img};
+      for (int s = 0; s < sh.npts; ++s) {
+        T.w64[s] = w[s];
+        T.w[s] = (float)w[s];
+      }
+      T.eq[0] = sh.q;
+      T.eqf[0] = (float)sh.q;
+      if (sh.nmov > 1) {
+        T.eq[1] = sh.qa_img;
+        T.eqf[1] = (float)sh.qa_img;
+      }
+    }
+  }
+  (void)W;
 }
 
 // All warps: traverse, then thread 0 assembles dE (FP64).  Requires a
@@ -97,39 +146,29 @@ __device__ __forceinline__ unsigned warp_points(int warp, int W, int npts) {
 template <int P, typename Real, int LAYOUT>
 __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
   MoveSh& sh = st.sh;
-  const int warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
   __syncthreads();
-  const unsigned pm = warp_points(warp, W, sh.npts);
   TravOut o;
-  o.sum = 0.0;
-  o.visited = o.accepted = o.pairs = o.fp64 = o.err = 0;
-  if (pm) warp_traverse<P, Real, LAYOUT>(S, sh.T, st.ws[warp], pm, record_path ? sh.path : nullptr, o);
-  if ((threadIdx.x & 31) == 0) {
-    sh.part[warp] = o.sum;
-    sh.cnt[warp][0] = o.visited;
-    sh.cnt[warp][1] = o.accepted;
-    sh.cnt[warp][2] = o.pairs;
-    sh.cnt[warp][3] = o.fp64;
-    sh.cnt[warp][4] = o.err;
-  }
-  __syncthreads();
+  block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr, o);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < W; ++w) s += sh.part[w];
+    double s = o.sum;
+    sh.cnt[0][0] = o.visited;
+    sh.cnt[0][1] = o.accepted;
+    sh.cnt[0][2] = o.pairs;
+    sh.cnt[0][3] = o.fp64;
+    sh.cnt[0][4] = o.err;
     if (sh.npts == 4) {
+      // ion-image pair terms q q'/|r - r'| at the new and old positions
+      const TravPts& T = sh.T;
       double pb, pa;
       if (sizeof(Real) == 4) {
-        const float2 bx = split2(sh.b[0]), by = split2(sh.b[1]), bz = split2(sh.b[2]);
-        const float2 ix = split2(sh.bi[0]), iy = split2(sh.bi[1]), iz = split2(sh.bi[2]);
-        const float2 ax = split2(sh.a[0]), ay = split2(sh.a[1]), az = split2(sh.a[2]);
-        const float2 jx = split2(sh.ai[0]), jy = split2(sh.ai[1]), jz = split2(sh.ai[2]);
-        float dx = (bx.x - ix.x) + (bx.y - ix.y), dy = (by.x - iy.x) + (by.y - iy.y),
-              dz = (bz.x - iz.x) + (bz.y - iz.y);
+        float dx = (T.hi[1][0] - T.hi[3][0]) + (T.lo[1][0] - T.lo[3][0]);
+        float dy = (T.hi[1][1] - T.hi[3][1]) + (T.lo[1][1] - T.lo[3][1]);
+        float dz = (T.hi[1][2] - T.hi[3][2]) + (T.lo[1][2] - T.lo[3][2]);
         pb = (double)((float)(sh.q * sh.qb_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
-        dx = (ax.x - jx.x) + (ax.y - jx.y);
-        dy = (ay.x - jy.x) + (ay.y - jy.y);
-        dz = (az.x - jz.x) + (az.y - jz.y);
+        dx = (T.hi[0][0] - T.hi[2][0]) + (T.lo[0][0] - T.lo[2][0]);
+        dy = (T.hi[0][1] - T.hi[2][1]) + (T.lo[0][1] - T.lo[2][1]);
+        dz = (T.hi[0][2] - T.hi[2][2]) + (T.lo[0][2] - T.lo[2][2]);
         pa = (double)((float)(sh.q * sh.qa_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
       } else {
         double dx = sh.b[0] - sh.bi[0], dy = sh.b[1] - sh.bi[1], dz = sh.b[2] - sh.bi[2];
@@ -142,15 +181,12 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
       s += pb - pa;
     }
     sh.dE = S.lB * s;
-    for (int w = 1; w < W; ++w)
-      for (int k = 0; k < 5; ++k)
-        sh.cnt[0][k] = (k == 4) ? max(sh.cnt[0][k], sh.cnt[w][k]) : sh.cnt[0][k] + sh.cnt[w][k];
   }
   __syncthreads();
 }
 
-// Complete the cluster paths of the four points by descending from the deepest
-// recorded cluster (threads 0..npts-1).
+// Complete the cluster paths of the points by descending from the deepest
+// recorded cluster, and read the path leaves' counts (threads 0..npts-1).
 static __device__ void complete_paths(const SysDev& S, MoveSh& sh) {
   const int s = threadIdx.x;
   if (s < sh.npts) {
@@ -158,24 +194,32 @@ static __device__ void complete_paths(const SysDev& S, MoveSh& sh) {
     if (sh.path[s][0] < 0) sh.path[s][0] = 0;
     while (d < S.Dmax && sh.path[s][d + 1] >= 0) ++d;
     int node = sh.path[s][d];
-    for (;;) {
-      const int fc = S.nB[node].x;
-      if (fc < 0 || d >= S.Dmax) break;
+    int4 b = S.nB[node];
+    while (b.x >= 0 && d < S.Dmax) {
       const int o = (int)((sh.T.pkey[s] >> (3 * (S.Dmax - d - 1))) & 7ULL);
-      node = fc + o;
+      node = b.x + o;
       ++d;
       sh.path[s][d] = node;
+      b = S.nB[node];
     }
     sh.plen[s] = d;
+    sh.leafcnt[s] = b.y;
   }
 }
 
-// Capacity rule (thread 0): after the move no depth-Dmax cell may hold more than C charges.
+// Capacity rule (thread 0): after the move no depth-Dmax cell may hold more
+// than C charges.  The common case is settled from the leaf counts alone.
 static __device__ bool capacity_violation(const SysDev& S, const MoveSh& sh) {
   for (int s = 1; s < sh.npts; s += 2) {
-    const unsigned long long kb = sh.T.pkey[s];
     const int L = sh.path[s][sh.plen[s]];
-    const int c = S.nB[L].y;
+    const int sh3 = 3 * (S.Dmax - sh.plen[s]);
+    const unsigned long long kL = sh.T.pkey[s] >> sh3;
+    int bound = sh.leafcnt[s];
+    for (int u = 1; u < sh.npts; u += 2) bound += ((sh.T.pkey[u] >> sh3) == kL) ? 1 : 0;
+    for (int u = 0; u < sh.T.n_excl; ++u) bound -= ((sh.T.ekey[u] >> sh3) == kL) ? 1 : 0;
+    if (bound <= S.C) continue;  // the whole leaf stays within capacity
+    const unsigned long long kb = sh.T.pkey[s];
+    const int c = sh.leafcnt[s];
     int n = 0;
     for (int k = 0; k < c; ++k) {
       const int j = __float_as_int(S.sB[L * (S.C + 2) + k].w);
@@ -245,113 +289,155 @@ static __device__ void merge_cluster(const SysDev& S, MoveSh& sh, int A) {
   *child_ptr(S, A) = -1;
 }
 
+// Leaf slot operations of the moved charges (thread 0), from the pre-move leaf
+// counts: delete = refill the slot with the leaf's last one, add = append.
+static __device__ void move_slots(const SysDev& S, MoveSh& sh) {
+  const int SC = S.C + 2;
+  int LA[2], LB[2], cA[2], cB[2];
+  for (int m = 0; m < sh.nmov; ++m) {
+    LA[m] = sh.path[2 * m][sh.plen[2 * m]];
+    LB[m] = sh.path[2 * m + 1][sh.plen[2 * m + 1]];
+    cA[m] = sh.leafcnt[2 * m];
+    cB[m] = sh.leafcnt[2 * m + 1];
+  }
+  if (sh.nmov > 1 && LA[0] != LB[0]) {  // leaf counts as the image sees them
+    cA[1] += (LA[1] == LB[0]) - (LA[1] == LA[0]);
+    cB[1] += (LB[1] == LB[0]) - (LB[1] == LA[0]);
+  }
+  int slot[2] = {sh.slot_i, sh.slot_img};
+  for (int m = 0; m < sh.nmov; ++m) {
+    const int j = m ? sh.img : sh.i;
+    const double* B_ = m ? sh.bi : sh.b;
+    const double qb = m ? sh.qb_img : sh.q;
+    const int pb = 2 * m + 1;
+    const float4 na4 = make_float4(sh.T.hi[pb][0], sh.T.hi[pb][1], sh.T.hi[pb][2], (float)qb);
+    const float4 nb4 = make_float4(sh.T.lo[pb][0], sh.T.lo[pb][1], sh.T.lo[pb][2], __int_as_float(j));
+    if (LA[m] == LB[m]) {
+      S.sA[LA[m] * SC + slot[m]] = na4;
+      S.sB[LA[m] * SC + slot[m]] = nb4;
+    } else {
+      const int k = slot[m], last = cA[m] - 1;
+      if (k != last) {
+        const float4 la = S.sA[LA[m] * SC + last], lb = S.sB[LA[m] * SC + last];
+        S.sA[LA[m] * SC + k] = la;
+        S.sB[LA[m] * SC + k] = lb;
+        const int moved = __float_as_int(lb.w);
+        S.slot_of[moved] = k;
+        if (m == 0 && sh.nmov > 1 && moved == sh.img) slot[1] = k;
+      }
+      S.sA[LB[m] * SC + cB[m]] = na4;
+      S.sB[LB[m] * SC + cB[m]] = nb4;
+      S.leaf_of[j] = LB[m];
+      S.slot_of[j] = cB[m];
+    }
+    S.px[j] = B_[0];
+    S.py[j] = B_[1];
+    S.pz[j] = B_[2];
+    S.pq[j] = qb;
+    S.ckey[j] = sh.T.pkey[pb];
+  }
+}
+
 // Local adjustment (Sec. 3.3) of an accepted move, all threads of the block.
-// Requires complete paths (complete_paths) and sh.T.pkey of the new points.
-static __device__ void commit_move_block(const SysDev& S, MoveSh& sh) {
-  const int K = S.K, SC = S.C + 2;
-  // (A) FP64 moments on both paths, per level: same cluster -> M += mb - ma,
-  // else M_old -= ma and M_new += mb.
+// Requires complete paths and leaf counts (complete_paths).
+static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
+  MoveSh& sh = st.sh;
+  const int K = S.K, SC = S.C + 2, P = S.p;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  constexpr int NL = BHMC_MAX_D + 1;
+  // (A0) powers (r - r_A)^k along both paths of both moved charges (FP64,
+  // built by repeated multiplication as in the definition of the moments)
+  for (int it = tid; it < sh.nmov * 2 * NL * 3; it += nth) {
+    const int ax = it % 3;
+    int r = it / 3;
+    const int d = r % NL;
+    r /= NL;
+    const int side = r & 1, m = r >> 1;
+    const int ps = 2 * m + side;
+    if (d > sh.plen[ps]) continue;
+    const float4 c = S.nA[sh.path[ps][d]];
+    const double* X = m ? (side ? sh.bi : sh.ai) : (side ? sh.b : sh.a);
+    const double diff = __dsub_rn(X[ax], (double)(ax == 0 ? c.x : (ax == 1 ? c.y : c.z)));
+    double* pw = st.pw[m][side][d][ax];
+    double v = 1.0;
+    pw[0] = v;
+    for (int k = 1; k <= P; ++k) {
+      v = __dmul_rn(v, diff);
+      pw[k] = v;
+    }
+  }
+  if (tid == 0) sh.slot_i = S.slot_of[sh.i];
+  if (tid == 1 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
+  if (tid < 2) sh.merge_d[tid] = 1 << 20;
+  __syncthreads();
+  // (A1) FP64 moments per level: same cluster -> M += mb - ma, else M_old -= ma
+  // and M_new += mb; ion first, image second (their paths share clusters).
+  // With the image's pass thread 0 moves the leaf slots and the other threads
+  // update the counts along the paths.
   for (int m = 0; m < sh.nmov; ++m) {
     const int pa = 2 * m, pb = 2 * m + 1;
     const int La = sh.plen[pa], Lb = sh.plen[pb];
     const int Dn = max(La, Lb) + 1;
     const double qa = m ? sh.qa_img : sh.q, qb = m ? sh.qb_img : sh.q;
-    const double* A_ = m ? sh.ai : sh.a;
-    const double* B_ = m ? sh.bi : sh.b;
-    for (int it = threadIdx.x; it < Dn * K; it += blockDim.x) {
+    for (int it = tid; it < Dn * K; it += nth) {
       const int d = it / K, t = it - d * K;
       const int na = d <= La ? sh.path[pa][d] : -1;
       const int nb = d <= Lb ? sh.path[pb][d] : -1;
-      int n1, n2, n3;
-      term_exponents(t, n1, n2, n3);
+      const int n1 = sh.ex[t][0], n2 = sh.ex[t][1], n3 = sh.ex[t][2];
+      double ma = 0.0, mb = 0.0;
+      if (na >= 0)
+        ma = __dmul_rn(qa, __dmul_rn(__dmul_rn(st.pw[m][0][d][0][n1], st.pw[m][0][d][1][n2]),
+                                     st.pw[m][0][d][2][n3]));
+      if (nb >= 0)
+        mb = __dmul_rn(qb, __dmul_rn(__dmul_rn(st.pw[m][1][d][0][n1], st.pw[m][1][d][1][n2]),
+                                     st.pw[m][1][d][2][n3]));
       if (na >= 0 && na == nb) {
-        const float4 c = S.nA[na];
-        const double ma = mono_term(n1, n2, n3, qa, __dsub_rn(A_[0], (double)c.x),
-                                    __dsub_rn(A_[1], (double)c.y), __dsub_rn(A_[2], (double)c.z));
-        const double mb = mono_term(n1, n2, n3, qb, __dsub_rn(B_[0], (double)c.x),
-                                    __dsub_rn(B_[1], (double)c.y), __dsub_rn(B_[2], (double)c.z));
         double* M = &S.M64[(size_t)na * K + t];
         *M = __dadd_rn(*M, __dsub_rn(mb, ma));
         mirror(S, na, t, *M);
       } else {
         if (na >= 0) {
-          const float4 c = S.nA[na];
-          const double ma = mono_term(n1, n2, n3, qa, __dsub_rn(A_[0], (double)c.x),
-                                      __dsub_rn(A_[1], (double)c.y), __dsub_rn(A_[2], (double)c.z));
           double* M = &S.M64[(size_t)na * K + t];
           *M = __dsub_rn(*M, ma);
           mirror(S, na, t, *M);
         }
         if (nb >= 0) {
-          const float4 c = S.nA[nb];
-          const double mb = mono_term(n1, n2, n3, qb, __dsub_rn(B_[0], (double)c.x),
-                                      __dsub_rn(B_[1], (double)c.y), __dsub_rn(B_[2], (double)c.z));
           double* M = &S.M64[(size_t)nb * K + t];
           *M = __dadd_rn(*M, mb);
           mirror(S, nb, t, *M);
         }
       }
     }
+    if (m == sh.nmov - 1) {
+      if (tid == 0) move_slots(S, sh);
+      for (int it = tid; it < sh.nmov * NL; it += nth) {
+        const int mm = it / NL, d = it - mm * NL;
+        const int pa2 = 2 * mm, pb2 = 2 * mm + 1;
+        const int na = d <= sh.plen[pa2] ? sh.path[pa2][d] : -1;
+        const int nb = d <= sh.plen[pb2] ? sh.path[pb2][d] : -1;
+        if (na != nb) {
+          if (na >= 0) atomicSub(count_ptr(S, na), 1);
+          if (nb >= 0) atomicAdd(count_ptr(S, nb), 1);
+        }
+      }
+    }
     __syncthreads();
   }
-  // (B) counts, leaf slots (delete = refill with the last slot, add = append), tracking
-  if (threadIdx.x == 0) {
-    for (int m = 0; m < sh.nmov; ++m) {
-      const int pa = 2 * m, pb = 2 * m + 1;
-      const int La = sh.plen[pa], Lb = sh.plen[pb];
-      const int j = m ? sh.img : sh.i;
-      const double* B_ = m ? sh.bi : sh.b;
-      const double qb = m ? sh.qb_img : sh.q;
-      for (int d = 0; d <= max(La, Lb); ++d) {
-        const int na = d <= La ? sh.path[pa][d] : -1;
-        const int nb = d <= Lb ? sh.path[pb][d] : -1;
-        if (na != nb) {
-          if (na >= 0) *count_ptr(S, na) -= 1;
-          if (nb >= 0) *count_ptr(S, nb) += 1;
-        }
-      }
-      const float2 fx = split2(B_[0]), fy = split2(B_[1]), fz = split2(B_[2]);
-      const float4 na4 = make_float4(fx.x, fy.x, fz.x, (float)qb);
-      const float4 nb4 = make_float4(fx.y, fy.y, fz.y, __int_as_float(j));
-      const int LA = sh.path[pa][La], LB = sh.path[pb][Lb];
-      if (LA == LB) {
-        const int k = S.slot_of[j];
-        S.sA[LA * SC + k] = na4;
-        S.sB[LA * SC + k] = nb4;
-      } else {
-        const int k = S.slot_of[j];
-        const int last = S.nB[LA].y;
-        if (k != last) {
-          const float4 la = S.sA[LA * SC + last], lb = S.sB[LA * SC + last];
-          S.sA[LA * SC + k] = la;
-          S.sB[LA * SC + k] = lb;
-          S.slot_of[__float_as_int(lb.w)] = k;
-        }
-        const int kk = S.nB[LB].y - 1;
-        S.sA[LB * SC + kk] = na4;
-        S.sB[LB * SC + kk] = nb4;
-        S.leaf_of[j] = LB;
-        S.slot_of[j] = kk;
-      }
-      S.px[j] = B_[0];
-      S.py[j] = B_[1];
-      S.pz[j] = B_[2];
-      S.pq[j] = qb;
-      S.ckey[j] = sh.T.pkey[pb];
-    }
-    // (C) merge the topmost internal cluster on an old path holding <= C charges
-    for (int m = 0; m < sh.nmov; ++m) {
-      const int pa = 2 * m;
-      for (int d = 0; d <= sh.plen[pa]; ++d) {
-        const int A = sh.path[pa][d];
-        if (d > 0 && S.nB[sh.path[pa][d - 1]].x != (A & ~7)) break;
-        const int4 b = S.nB[A];
-        if (b.x < 0) break;
-        if (b.y <= S.C) {
-          merge_cluster(S, sh, A);
-          break;
-        }
-      }
+  // (C) merge the topmost internal cluster on an old path holding <= C charges
+  for (int it = tid; it < sh.nmov * NL; it += nth) {
+    const int m = it / NL, d = it - m * NL;
+    if (d > sh.plen[2 * m]) continue;
+    const int4 b = S.nB[sh.path[2 * m][d]];
+    if (b.x >= 0 && b.y <= S.C) atomicMin(&sh.merge_d[m], d);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int d0 = sh.merge_d[0];
+    if (d0 < NL) merge_cluster(S, sh, sh.path[0][d0]);
+    if (sh.nmov > 1) {
+      const int d1 = sh.merge_d[1];
+      const bool inside = d0 < NL && d1 >= d0 && sh.path[2][d0] == sh.path[0][d0];
+      if (d1 < NL && !inside) merge_cluster(S, sh, sh.path[2][d1]);
     }
   }
   __syncthreads();
@@ -359,7 +445,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveSh& sh) {
   for (int m = 0; m < sh.nmov; ++m) {
     const int j = m ? sh.img : sh.i;
     for (int guard = 0; guard <= BHMC_MAX_D; ++guard) {
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         const int L = S.leaf_of[j];
         const int4 b = S.nB[L];
         const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
@@ -400,13 +486,12 @@ static __device__ void commit_move_block(const SysDev& S, MoveSh& sh) {
       }
       __syncthreads();
       if (sh.split_node < 0) break;
-      for (int it = threadIdx.x; it < 8 * K; it += blockDim.x) {
+      for (int it = tid; it < 8 * K; it += nth) {
         const int o = it / K, t = it - o * K;
         const int ch = sh.split_g + o;
         const float4 c = S.nA[ch];
         const int cnt = S.nB[ch].y;
-        int n1, n2, n3;
-        term_exponents(t, n1, n2, n3);
+        const int n1 = sh.ex[t][0], n2 = sh.ex[t][1], n3 = sh.ex[t][2];
         double M = 0.0;
         for (int k = 0; k < cnt; ++k) {
           const int idx = __float_as_int(S.sB[ch * SC + k].w);
@@ -449,7 +534,8 @@ struct MoveRec {
   int outcome, flagged;
 };
 
-// One full trial move m of a chain (all threads).  Returns the outcome.
+// One full trial move m of a chain (all threads).  Returns the outcome, or -1
+// after a device error (recorded in S.err).
 template <int P, typename Real, int LAYOUT>
 __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica,
                        uint2 key, double step, MoveRec* rec) {
@@ -459,21 +545,21 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
     const uint4 v = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 1u), key);
     const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
     const unsigned uu[3] = {u.y, u.z, u.w};
-    double b[3];
     const double src[3] = {S.px[i], S.py[i], S.pz[i]};
     for (int k = 0; k < 3; ++k) {
       const double delta =
           __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)uu[k], 0x1p-32), 0x1p-33), 0.5), step);
-      b[k] = __dadd_rn(src[k], delta);
+      sh.b[k] = __dadd_rn(src[k], delta);
     }
-    sh.outcome = setup_move(S, sh, i, b);
+    sh.i = i;
     sh.dE = 0.0;
     sh.flagged = 0;
     sh.alpha = __dmul_rn(__dadd_rn((double)v.x, 0.5), 0x1p-32);
-    sh.go = (sh.outcome < 0);
   }
   __syncthreads();
-  if (sh.go) {
+  setup_move(S, sh);
+  __syncthreads();
+  if (sh.outcome < 0) {
     eval_move<P, Real, LAYOUT>(S, st, true);
     if (sh.cnt[0][4]) {
       if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
@@ -494,7 +580,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
     }
     __syncthreads();
     if (sh.outcome == BHMC_ACCEPT) {
-      commit_move_block(S, sh);
+      commit_move_block(S, st);
       if (threadIdx.x == 0) *S.energy += sh.dE;
     }
   }
@@ -535,13 +621,19 @@ __global__ void __launch_bounds__(128) k_delta(SysDev S, int i, double bx, doubl
                                                DeltaOut* out) {
   __shared__ MoveStore st;
   if (threadIdx.x == 0) {
-    const double b[3] = {bx, by, bz};
-    const int o = setup_move(S, st.sh, i, b);
-    st.sh.go = o < 0;
-    out->status = o < 0 ? 0 : (o == BHMC_REJECT_DOMAIN ? BHMC_EDOMAIN : BHMC_EOVERLAP);
+    st.sh.i = i;
+    st.sh.b[0] = bx;
+    st.sh.b[1] = by;
+    st.sh.b[2] = bz;
   }
   __syncthreads();
-  if (!st.sh.go) return;
+  setup_move(S, st.sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int o = st.sh.outcome;
+    out->status = o < 0 ? 0 : (o == BHMC_REJECT_DOMAIN ? BHMC_EDOMAIN : BHMC_EOVERLAP);
+  }
+  if (st.sh.outcome >= 0) return;
   eval_move<P, Real, LAYOUT>(S, st, false);
   if (threadIdx.x == 0) {
     out->dE = st.sh.dE;
@@ -556,6 +648,7 @@ __global__ void __launch_bounds__(128) k_step(SysDev S, unsigned long long m, un
                                               bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   if (*(volatile int*)S.err) return;
+  init_tables(st.sh, S.K);
   const int o = mc_move<P, Real, LAYOUT>(S, st, m, replica, key, step, recs);
   if (threadIdx.x == 0 && o >= 0) {
     tally(stats, o, st.sh.flagged);
@@ -575,6 +668,7 @@ __global__ void __launch_bounds__(128) k_batch(const SysDev* views, int n_rep, c
   __shared__ MoveStore st;
   __shared__ int rep;
   __shared__ SysDev S;
+  init_tables(st.sh, nterms(P));
   for (;;) {
     if (threadIdx.x == 0) rep = atomicAdd(next, 1);
     __syncthreads();
@@ -612,14 +706,16 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, double* partial, int* 
   double acc = 0.0;
   for (int j = blockIdx.x * W + warp; j < S.n_tot; j += gridDim.x * W) {
     TravPts& T = Tw[warp];
-    if (lane == 0) {
-      const double x[3] = {S.px[j], S.py[j], S.pz[j]};
-      for (int k = 0; k < 3; ++k) {
-        T.x[0][k] = x[k];
-        const float2 f = split2(x[k]);
-        T.hi[0][k] = f.x;
-        T.lo[0][k] = f.y;
-      }
+    if (lane < 3) {
+      const double x = lane == 0 ? S.px[j] : (lane == 1 ? S.py[j] : S.pz[j]);
+      const float2 f = split2(x);
+      T.x[0][lane] = x;
+      T.hi[0][lane] = f.x;
+      T.lo[0][lane] = f.y;
+      T.ex[0][lane] = x;
+      T.ehi[0][lane] = f.x;
+      T.elo[0][lane] = f.y;
+    } else if (lane == 3) {
       T.w[0] = 1.0f;
       T.w64[0] = 1.0;
       T.pkey[0] = 0ULL;
@@ -627,9 +723,7 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, double* partial, int* 
       T.excl[0] = j;
       T.ekey[0] = S.ckey[j];
       T.eq[0] = S.pq[j];
-      T.ex[0][0] = x[0];
-      T.ex[0][1] = x[1];
-      T.ex[0][2] = x[2];
+      T.eqf[0] = (float)S.pq[j];
     }
     __syncwarp();
     TravOut o;

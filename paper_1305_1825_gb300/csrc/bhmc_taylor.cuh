@@ -51,57 +51,4 @@ __device__ __forceinline__ void taylor(R x, R y, R z, R (&T)[nterms(P)]) {
   }
 }
 
-// sum_n T_n M_n with M read from the FP32 mirror of one node.
-template <int P, int LAYOUT>
-__device__ __forceinline__ float multipole_f32(const SysDev& S, int node, float x, float y,
-                                               float z) {
-  constexpr int K = nterms(P);
-  float T[K];
-  taylor<P, float>(x, y, z, T);
-  float v = 0.f;
-  if (LAYOUT == BHMC_LAYOUT_AOS) {
-    constexpr int KP = pad4(K);
-    const float4* M4 = reinterpret_cast<const float4*>(S.M32 + (size_t)node * KP);
-#pragma unroll
-    for (int t4 = 0; t4 < KP / 4; ++t4) {
-      float4 m = M4[t4];
-      const float mm[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (4 * t4 + u < K) v = fmaf(T[4 * t4 + u], mm[u], v);
-    }
-  } else {
-    const float* M = S.M32 + node;
-#pragma unroll
-    for (int t = 0; t < K; ++t) v = fmaf(T[t], M[(size_t)t * S.node_cap], v);
-  }
-  return v;
-}
-
-// Same with moments given explicitly (FP64 master minus excluded charges).
-template <int P, typename R>
-__device__ __forceinline__ R multipole_explicit(R x, R y, R z, const double* M) {
-  constexpr int K = nterms(P);
-  R T[K];
-  taylor<P, R>(x, y, z, T);
-  R v = R(0);
-#pragma unroll
-  for (int t = 0; t < K; ++t) v += T[t] * R(M[t]);
-  return v;
-}
-
-// FP64 master moments read directly (all-FP64 mode).
-template <int P>
-__device__ __forceinline__ double multipole_f64(const SysDev& S, int node, double x, double y,
-                                                double z) {
-  constexpr int K = nterms(P);
-  double T[K];
-  taylor<P, double>(x, y, z, T);
-  const double* M = S.M64 + (size_t)node * K;
-  double v = 0.0;
-#pragma unroll
-  for (int t = 0; t < K; ++t) v += T[t] * M[t];
-  return v;
-}
-
 }  // namespace bhmc

@@ -28,11 +28,13 @@ struct TravPts {
   unsigned long long ekey[2];
   double eq[2];
   double ex[2][3];
+  float ehi[2][3], elo[2][3];  // excluded positions as float pairs
+  float eqf[2];
 };
 
 struct WarpStore {
   uint2 stk[BHMC_STACK];
-  unsigned mi[128];        // multipole items: node << 3 | corrected << 2 | point
+  unsigned mi[128];        // multipole items: node << 4 | excluded-inside mask << 2 | point
   uint2 di[32];            // direct items: {leaf, count << 4 | point mask}
 };
 
@@ -83,47 +85,86 @@ __device__ __forceinline__ bool mac_test<double>(const SysDev& S, const float4& 
   return r2 <= __dmul_rn(S.theta2, dd);
 }
 
-// Moments of `node` minus the terms of the excluded charges inside it (FP64).
-static __device__ __noinline__ void corrected_moments(const SysDev& S, const TravPts& T, int node,
-                                               double* M) {
-  const float4 a = S.nA[node];
-  const int4 b = S.nB[node];
-  const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-  const int sh = 3 * (S.Dmax - key_depth(key));
-  for (int t = 0; t < S.K; ++t) M[t] = S.M64[(size_t)node * S.K + t];
-  for (int k = 0; k < T.n_excl; ++k) {
-    if ((T.ekey[k] >> sh) != key) continue;
-    const double dx = __dsub_rn(T.ex[k][0], (double)a.x);
-    const double dy = __dsub_rn(T.ex[k][1], (double)a.y);
-    const double dz = __dsub_rn(T.ex[k][2], (double)a.z);
-    for (int t = 0; t < S.K; ++t) {
-      int n1, n2, n3;
-      term_exponents(t, n1, n2, n3);
-      M[t] = __dsub_rn(M[t], mono_term(n1, n2, n3, T.eq[k], dx, dy, dz));
-    }
+// sum_n T_n d^n for a point at offset d from the cluster centre: the p-th
+// order expansion of 1/|x - r| for a single charge.
+template <int P, typename R>
+__device__ __forceinline__ R dot_monomials(const R (&T)[nterms(P)], R dx, R dy, R dz) {
+  R px[P + 1], py[P + 1], pz[P + 1];
+  px[0] = py[0] = pz[0] = R(1);
+#pragma unroll
+  for (int k = 1; k <= P; ++k) {
+    px[k] = px[k - 1] * dx;
+    py[k] = py[k - 1] * dy;
+    pz[k] = pz[k - 1] * dz;
   }
+  R v = R(0);
+#pragma unroll
+  for (int k = 0; k <= P; ++k)
+#pragma unroll
+    for (int n1 = k; n1 >= 0; --n1)
+#pragma unroll
+      for (int n2 = k - n1; n2 >= 0; --n2) v += T[tidx(n1, n2, k - n1 - n2)] * (px[n1] * py[n2] * pz[k - n1 - n2]);
+  return v;
 }
 
+// Multipole term of cluster `node` at point s: sum_n T_n(r_A - x) M'_n with
+// M' = M minus the terms of the excluded charges inside the cluster (emask);
+// the excluded charges' own expansions are subtracted explicitly.
 template <int P, typename Real, int LAYOUT>
 __device__ __forceinline__ Real eval_item(const SysDev& S, const TravPts& T, int node, int s,
-                                          bool corr) {
+                                          unsigned emask) {
+  constexpr int K = nterms(P);
   const float4 a = S.nA[node];
   if (sizeof(Real) == 4) {
     const float rx = (a.x - T.hi[s][0]) - T.lo[s][0];
     const float ry = (a.y - T.hi[s][1]) - T.lo[s][1];
     const float rz = (a.z - T.hi[s][2]) - T.lo[s][2];
-    if (!corr) return (Real)multipole_f32<P, LAYOUT>(S, node, rx, ry, rz);
-    double M[nterms(P)];
-    corrected_moments(S, T, node, M);
-    return (Real)multipole_explicit<P, float>(rx, ry, rz, M);
+    float Tc[K];
+    taylor<P, float>(rx, ry, rz, Tc);
+    float v = 0.f;
+    if (LAYOUT == BHMC_LAYOUT_AOS) {
+      constexpr int KP = pad4(K);
+      const float4* M4 = reinterpret_cast<const float4*>(S.M32 + (size_t)node * KP);
+#pragma unroll
+      for (int t4 = 0; t4 < KP / 4; ++t4) {
+        const float4 m = M4[t4];
+        const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * t4 + u < K) v = fmaf(Tc[4 * t4 + u], mm[u], v);
+      }
+    } else {
+      const float* M = S.M32 + node;
+#pragma unroll
+      for (int t = 0; t < K; ++t) v = fmaf(Tc[t], M[(size_t)t * S.node_cap], v);
+    }
+    while (emask) {
+      const int k = __ffs(emask) - 1;
+      emask &= emask - 1;
+      const float dx = (T.ehi[k][0] - a.x) + T.elo[k][0];
+      const float dy = (T.ehi[k][1] - a.y) + T.elo[k][1];
+      const float dz = (T.ehi[k][2] - a.z) + T.elo[k][2];
+      v -= T.eqf[k] * dot_monomials<P, float>(Tc, dx, dy, dz);
+    }
+    return (Real)v;
   } else {
     const double rx = __dsub_rn((double)a.x, T.x[s][0]);
     const double ry = __dsub_rn((double)a.y, T.x[s][1]);
     const double rz = __dsub_rn((double)a.z, T.x[s][2]);
-    if (!corr) return (Real)multipole_f64<P>(S, node, rx, ry, rz);
-    double M[nterms(P)];
-    corrected_moments(S, T, node, M);
-    return (Real)multipole_explicit<P, double>(rx, ry, rz, M);
+    double Tc[K];
+    taylor<P, double>(rx, ry, rz, Tc);
+    const double* M = S.M64 + (size_t)node * K;
+    double v = 0.0;
+#pragma unroll
+    for (int t = 0; t < K; ++t) v += Tc[t] * M[t];
+    while (emask) {
+      const int k = __ffs(emask) - 1;
+      emask &= emask - 1;
+      v -= T.eq[k] * dot_monomials<P, double>(Tc, __dsub_rn(T.ex[k][0], (double)a.x),
+                                               __dsub_rn(T.ex[k][1], (double)a.y),
+                                               __dsub_rn(T.ex[k][2], (double)a.z));
+    }
+    return (Real)v;
   }
 }
 
@@ -148,83 +189,108 @@ struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+// Direct terms of one leaf slot against the points of `m`.
+template <typename Real>
+__device__ __forceinline__ void direct_slot(const SysDev& S, const TravPts& T, float4 sa, float4 sb,
+                                            unsigned m, Acc<Real>& acc, int& pairs) {
+  const int j = __float_as_int(sb.w);
+  for (int u = 0; u < T.n_excl; ++u)
+    if (T.excl[u] == j) return;
+  while (m) {
+    const int s = __ffs(m) - 1;
+    m &= m - 1;
+    if (sizeof(Real) == 4) {
+      const float dx = (sa.x - T.hi[s][0]) + (sb.x - T.lo[s][0]);
+      const float dy = (sa.y - T.hi[s][1]) + (sb.y - T.lo[s][1]);
+      const float dz = (sa.z - T.hi[s][2]) + (sb.z - T.lo[s][2]);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      acc.add((Real)(T.w[s] * (sa.w * rsqrtf(r2))));
+    } else {
+      const double dx = __dsub_rn(S.px[j], T.x[s][0]);
+      const double dy = __dsub_rn(S.py[j], T.x[s][1]);
+      const double dz = __dsub_rn(S.pz[j], T.x[s][2]);
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      acc.add((Real)(T.w64[s] * (S.pq[j] / r)));
+    }
+    ++pairs;
+  }
+}
+
 // Traverse from the root for the points in `pmask`; `path` (may be null)
-// receives, per point and level, the cluster containing the point.
+// receives, per point and level, the cluster containing the point.  The
+// headers of the next round's clusters are loaded before the current round's
+// multipole and direct terms are evaluated, so their latency overlaps compute.
 template <int P, typename Real, int LAYOUT>
 __device__ void warp_traverse(const SysDev& S, const TravPts& T, WarpStore& W, unsigned pmask,
                               int (*path)[BHMC_MAX_D + 1], TravOut& out) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  if (lane == 0) W.stk[0] = make_uint2(0u, pmask);
-  int top = 1;
-  __syncwarp();
+  const int g = lane >> 3;
   Acc<Real> acc;
   int visited = 0, accepted = 0, pairs = 0, fp64 = 0, err = 0;
   int cp = 1;
   while (cp < S.C) cp <<= 1;
   const int lg = 31 - __clz(cp);
+  const int SC = S.C + 2;
+  // first round: the root group {root, 7 empty slots}
+  int top = 0;
+  int npop = 1;
+  uint2 e = make_uint2(0u, g == 0 ? pmask : 0u);
+  int4 b = make_int4(-1, 0, 0, 0);
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (g == 0) {
+    b = S.nB[lane & 7];
+    a = S.nA[lane & 7];
+  }
   int rounds = 0;
-  while (top > 0) {
+  while (npop > 0) {
     if (++rounds > (1 << 22)) {
       err = BHMC_ETIMEOUT;
       break;
     }
-    const int npop = min(top, 4);
-    const int g = lane >> 3;
-    uint2 e = make_uint2(0u, 0u);
-    if (g < npop) e = W.stk[top - 1 - g];
-    __syncwarp();
-    top -= npop;
     const int node = (int)e.x + (lane & 7);
     const unsigned om = e.y & 15u, fd = (e.y >> 4) & 15u;
-    unsigned mac = 0, open = 0, fdc = 0, dir = 0;
+    unsigned mac = 0, open = 0, fdc = 0, dir = 0, emask = 0;
     int fc = -1, cnt = 0;
-    bool corr = false;
-    if (g < npop && (om | fd)) {
-      const int4 b = S.nB[node];
-      const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-      if (key != 0ULL) {
-        fc = b.x;
-        cnt = b.y;
-        const int d = key_depth(key);
-        const int sh = 3 * (S.Dmax - d);
-        int in_s = 0;
-        for (int k = 0; k < T.n_excl; ++k) in_s += ((T.ekey[k] >> sh) == key) ? 1 : 0;
-        if (path) {
-          unsigned all = om | fd;
-          while (all) {
-            const int s = __ffs(all) - 1;
-            all &= all - 1;
-            if ((T.pkey[s] >> sh) == key) path[s][d] = node;
-          }
+    const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
+    if (g < npop && (om | fd) && key != 0ULL) {
+      fc = b.x;
+      cnt = b.y;
+      const int d = key_depth(key);
+      const int sh = 3 * (S.Dmax - d);
+      for (int k = 0; k < T.n_excl; ++k) emask |= ((T.ekey[k] >> sh) == key) ? (1u << k) : 0u;
+      if (path) {
+        unsigned all = om | fd;
+        while (all) {
+          const int s = __ffs(all) - 1;
+          all &= all - 1;
+          if ((T.pkey[s] >> sh) == key) path[s][d] = node;
         }
-        visited += __popc(om);
-        const int np = cnt - in_s;
-        corr = in_s > 0;
-        if (np > 0) {
-          const float4 a = S.nA[node];
-          unsigned m = om;
-          while (m) {
-            const int s = __ffs(m) - 1;
-            m &= m - 1;
-            const unsigned bit = 1u << s;
-            if (np >= S.N0 && mac_test<Real>(S, a, T, s, fp64))
-              mac |= bit;
-            else if (fc >= 0)
-              (np > S.N0 ? open : fdc) |= bit;
-            else
-              dir |= bit;
-          }
-          if (fd) {
-            if (fc >= 0)
-              fdc |= fd;
-            else
-              dir |= fd;
-          }
+      }
+      visited += __popc(om);
+      const int np = cnt - __popc(emask);
+      if (np > 0) {
+        unsigned m = om;
+        while (m) {
+          const int s = __ffs(m) - 1;
+          m &= m - 1;
+          const unsigned bit = 1u << s;
+          if (np >= S.N0 && mac_test<Real>(S, a, T, s, fp64))
+            mac |= bit;
+          else if (fc >= 0)
+            (np > S.N0 ? open : fdc) |= bit;
+          else
+            dir |= bit;
+        }
+        if (fd) {
+          if (fc >= 0)
+            fdc |= fd;
+          else
+            dir |= fd;
         }
       }
     }
-    // children to the stack
+    // children to the stack (the popped entries' slots are reused)
     const bool push = (open | fdc) != 0;
     const unsigned pb = __ballot_sync(FULL, push);
     const int npush = __popc(pb);
@@ -234,7 +300,7 @@ __device__ void warp_traverse(const SysDev& S, const TravPts& T, WarpStore& W, u
     }
     if (push) W.stk[top + __popc(pb & lanemask_lt())] = make_uint2((unsigned)fc, open | (fdc << 4));
     top += npush;
-    // multipole items
+    // multipole and direct items of this round
     const int nm = __popc(mac);
     int incl = nm;
 #pragma unroll
@@ -249,60 +315,63 @@ __device__ void warp_traverse(const SysDev& S, const TravPts& T, WarpStore& W, u
       while (m) {
         const int s = __ffs(m) - 1;
         m &= m - 1;
-        W.mi[pos++] = ((unsigned)node << 3) | (corr ? 4u : 0u) | (unsigned)s;
+        W.mi[pos++] = ((unsigned)node << 4) | (emask << 2) | (unsigned)s;
       }
     }
     accepted += nm;
-    // direct items
     const unsigned db = __ballot_sync(FULL, dir != 0);
     const int ndir = __popc(db);
     if (dir) W.di[__popc(db & lanemask_lt())] = make_uint2((unsigned)node, ((unsigned)cnt << 4) | dir);
     __syncwarp();
+    // next round: pop and prefetch its headers
+    const int npop_n = min(top, 4);
+    uint2 e_n = make_uint2(0u, 0u);
+    int4 b_n = make_int4(-1, 0, 0, 0);
+    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g < npop_n) {
+      e_n = W.stk[top - 1 - g];
+      const int nn = (int)e_n.x + (lane & 7);
+      b_n = S.nB[nn];
+      a_n = S.nA[nn];
+    }
+    top -= npop_n;
+    // first direct pass: issue its loads before the multipole work
+    const int per = 32 >> lg;
+    const int kk = lane & (cp - 1);
+    uint2 di0 = make_uint2(0u, 0u);
+    float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
+    bool have0 = false;
+    if ((lane >> lg) < ndir) {
+      di0 = W.di[lane >> lg];
+      if (kk < (int)(di0.y >> 4)) {
+        const int slot = (int)di0.x * SC + kk;
+        sa0 = S.sA[slot];
+        sb0 = S.sB[slot];
+        have0 = true;
+      }
+    }
     for (int k = lane; k < total; k += 32) {
       const unsigned it = W.mi[k];
       const int s = (int)(it & 3u);
-      const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 3), s, (it & 4u) != 0);
+      const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
       acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
     }
-    const int per = 32 >> lg;
-    for (int base = 0; base < ndir; base += per) {
+    if (have0) direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
+    for (int base = per; base < ndir; base += per) {
       const int item = base + (lane >> lg);
-      const int k = lane & (cp - 1);
       if (item < ndir) {
         const uint2 di = W.di[item];
-        const int c = (int)(di.y >> 4);
-        if (k < c) {
-          const int slot = (int)di.x * (S.C + 2) + k;
-          const float4 sa = S.sA[slot];
-          const float4 sb = S.sB[slot];
-          const int j = __float_as_int(sb.w);
-          bool skip = false;
-          for (int u = 0; u < T.n_excl; ++u) skip |= (T.excl[u] == j);
-          if (!skip) {
-            unsigned m = di.y & 15u;
-            while (m) {
-              const int s = __ffs(m) - 1;
-              m &= m - 1;
-              if (sizeof(Real) == 4) {
-                const float dx = (sa.x - T.hi[s][0]) + (sb.x - T.lo[s][0]);
-                const float dy = (sa.y - T.hi[s][1]) + (sb.y - T.lo[s][1]);
-                const float dz = (sa.z - T.hi[s][2]) + (sb.z - T.lo[s][2]);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                acc.add((Real)(T.w[s] * (sa.w * rsqrtf(r2))));
-              } else {
-                const double dx = __dsub_rn(S.px[j], T.x[s][0]);
-                const double dy = __dsub_rn(S.py[j], T.x[s][1]);
-                const double dz = __dsub_rn(S.pz[j], T.x[s][2]);
-                const double r = sqrt(dx * dx + dy * dy + dz * dz);
-                acc.add((Real)(T.w64[s] * (S.pq[j] / r)));
-              }
-              ++pairs;
-            }
-          }
+        if (kk < (int)(di.y >> 4)) {
+          const int slot = (int)di.x * SC + kk;
+          direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
         }
       }
     }
     __syncwarp();
+    e = e_n;
+    b = b_n;
+    a = a_n;
+    npop = npop_n;
   }
   double v = acc.value();
 #pragma unroll
