@@ -39,8 +39,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--C", type=int, default=8)
-    ap.add_argument("--warps", type=int, default=4)
-    ap.add_argument("--layout", default="soa", choices=["soa", "aos"])
+    ap.add_argument("--warps", type=int, default=8)
+    ap.add_argument("--layout", default="aos", choices=["soa", "aos"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()

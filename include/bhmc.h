@@ -71,7 +71,7 @@ typedef struct {
   int32_t images;     /* 1: each mobile ion carries an image at R^2 r/|r|^2, charge alpha q R/|r| */
   double image_R, image_alpha;
   int32_t precision;  /* BHMC_PREC_F32 (FP32 traversal, FP64 moments) or BHMC_PREC_F64 (all FP64) */
-  int32_t warps;      /* warps cooperating on one move: 1, 2 or 4 (4 needs images) */
+  int32_t warps;      /* warps cooperating on one move: 1, 2, 4 or 8 */
   int32_t layout;     /* BHMC_LAYOUT_SOA or BHMC_LAYOUT_AOS for the FP32 moment mirror */
   double node_factor; /* node pool = 64 + node_factor * charges (0 selects 2.0) */
 } bhmc_params;

@@ -106,7 +106,7 @@ static bhmc_status validate(const bhmc_params* P) {
   if (P->images && !(P->image_R > 0.0)) return BHMC_EINVAL;
   if (P->precision != BHMC_PREC_F32 && P->precision != BHMC_PREC_F64) return BHMC_EINVAL;
   if (P->layout != BHMC_LAYOUT_SOA && P->layout != BHMC_LAYOUT_AOS) return BHMC_EINVAL;
-  if (P->warps != 1 && P->warps != 2 && P->warps != 4) return BHMC_EINVAL;
+  if (P->warps != 1 && P->warps != 2 && P->warps != 4 && P->warps != 8) return BHMC_EINVAL;
   if (P->node_factor < 0.0) return BHMC_EINVAL;
   return BHMC_OK;
 }
@@ -518,7 +518,7 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E) {
 }
 
 static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, int* err) {
-  const int w = 4;
+  const int w = BHMC_ENERGY_WARPS;
   switch (c->P.p) {
     case 2: return launch_energy<2>(c->S, w, grid, partial, err, c->stream);
     case 4: return launch_energy<4>(c->S, w, grid, partial, err, c->stream);
@@ -530,7 +530,7 @@ bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
   if (!E) return BHMC_EINVAL;
-  const int warps = 4;
+  const int warps = BHMC_ENERGY_WARPS;
   int grid = (ctx->S.n_tot + warps - 1) / warps;
   grid = std::min(grid, 152 * 16);
   double* partial = nullptr;

@@ -16,6 +16,33 @@
 
 namespace bhmc {
 
+// Loads issued at a fixed point of the instruction stream (the traversal
+// pipelines them one round ahead) and L2 prefetches of whole lines.
+__device__ __forceinline__ int4 ld_int4(const int4* p) {
+  int4 v;
+  asm volatile("ld.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_float4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Lines of [p, p + bytes) into L1.
+__device__ __forceinline__ void prefetch_range(const void* p, int bytes) {
+  const char* c = reinterpret_cast<const char*>(p);
+  for (int o = 0; o < bytes; o += 128) prefetch_l1(c + o);
+  prefetch_l1(c + bytes - 1);
+}
+
 struct BlockStore {
   uint2 stk[BHMC_BSTACK];
   unsigned mi[4 * 32 * BHMC_MAX_WARPS];  // node << 4 | excluded mask << 2 | point
@@ -25,9 +52,11 @@ struct BlockStore {
   int wred[BHMC_MAX_WARPS][5];
 };
 
+// `path` (may be null) receives per point and level the cluster containing the
+// point; `leafcnt[s]` the count of point s's leaf when the traversal reaches it.
 template <int P, typename Real, int LAYOUT>
 __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B, unsigned pmask,
-                               int (*path)[BHMC_MAX_D + 1], TravOut& out) {
+                               int (*path)[BHMC_MAX_D + 1], int* leafcnt, TravOut& out) {
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nth = blockDim.x, NW = nth >> 5, G = nth >> 3;
@@ -44,8 +73,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   int4 b = make_int4(-1, 0, 0, 0);
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (g == 0) {
-    b = S.nB[tid & 7];
-    a = S.nA[tid & 7];
+    b = ld_int4(S.nB + (tid & 7));
+    a = ld_float4(S.nA + (tid & 7));
   }
   int rounds = 0;
   while (npop > 0) {
@@ -65,33 +94,63 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       const int sh = 3 * (S.Dmax - d);
       for (int k = 0; k < T.n_excl; ++k) emask |= ((T.ekey[k] >> sh) == key) ? (1u << k) : 0u;
       if (path) {
-        unsigned all = om | fd;
-        while (all) {
-          const int s = __ffs(all) - 1;
-          all &= all - 1;
-          if ((T.pkey[s] >> sh) == key) path[s][d] = node;
+        const unsigned all = om | fd;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (((all >> s) & 1u) && (T.pkey[s] >> sh) == key) {
+            path[s][d] = node;
+            if (fc < 0) leafcnt[s] = cnt;
+          }
         }
       }
       visited += __popc(om);
       const int np = cnt - __popc(emask);
       if (np > 0) {
-        unsigned m = om;
-        while (m) {
-          const int s = __ffs(m) - 1;
-          m &= m - 1;
-          const unsigned bit = 1u << s;
-          if (np >= S.N0 && mac_test<Real>(S, a, T, s, fp64))
-            mac |= bit;
-          else if (fc >= 0)
-            (np > S.N0 ? open : fdc) |= bit;
-          else
-            dir |= bit;
+        // MAC for the four points at once (independent chains, predicated)
+        unsigned acc4 = 0, amb4 = 0;
+        if (sizeof(Real) == 4) {
+          const float rho2 = 3.0f * a.w * a.w;
+          const float hi_t = rho2 * 1.0000076293945312f, lo_t = rho2 * 0.9999923706054688f;
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const float4 h = T.h4[s], l = T.l4[s];
+            const float rx = (a.x - h.x) - l.x, ry = (a.y - h.y) - l.y, rz = (a.z - h.z) - l.z;
+            const float tt = S.theta2f * (rx * rx + ry * ry + rz * rz);
+            acc4 |= (tt >= hi_t) ? (1u << s) : 0u;
+            amb4 |= (tt > lo_t && tt < hi_t) ? (1u << s) : 0u;
+          }
+          amb4 &= om;
+          while (amb4) {  // within 2^-17 of the threshold: exact FP64 decision
+            const int s = __ffs(amb4) - 1;
+            amb4 &= amb4 - 1;
+            if (mac_test<double>(S, a, T, s, fp64)) acc4 |= 1u << s;
+            ++fp64;
+          }
+        } else {
+          unsigned m = om;
+          while (m) {
+            const int s = __ffs(m) - 1;
+            m &= m - 1;
+            if (mac_test<double>(S, a, T, s, fp64)) acc4 |= 1u << s;
+          }
         }
-        if (fd) {
-          if (fc >= 0)
-            fdc |= fd;
+        const unsigned ok = (np >= S.N0) ? acc4 & om : 0u;
+        const unsigned rest = om & ~ok;
+        mac = ok;
+        if (fc >= 0) {
+          if (np > S.N0)
+            open = rest;
           else
-            dir |= fd;
+            fdc = rest;
+          fdc |= fd;
+        } else {
+          dir = rest | fd;
+        }
+        if (LAYOUT == BHMC_LAYOUT_AOS && mac)
+          prefetch_range(S.M32 + (size_t)node * pad4(nterms(P)), pad4(nterms(P)) * 4);
+        if (dir) {
+          prefetch_range(S.sA + (size_t)node * SC, cnt * 16);
+          prefetch_range(S.sB + (size_t)node * SC, cnt * 16);
         }
       }
     }
@@ -150,8 +209,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     if (g < npop_n) {
       e_n = B.stk[top - 1 - g];
       const int nn = (int)e_n.x + (tid & 7);
-      b_n = S.nB[nn];
-      a_n = S.nA[nn];
+      b_n = ld_int4(S.nB + nn);
+      a_n = ld_float4(S.nA + nn);
     }
     top -= npop_n;
     // first direct pass: issue its loads before the multipole work
@@ -186,12 +245,15 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         }
       }
     }
-    __syncthreads();
+    // No barrier here: the next round writes the stack, the item lists and the
+    // per-warp counts only after its first barrier, which every thread reaches
+    // after finishing this round's items.
     e = e_n;
     b = b_n;
     a = a_n;
     npop = npop_n;
   }
+  __syncthreads();
   // block reductions (result valid in thread 0)
   double v = acc.value();
 #pragma unroll

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_moments_big(SysDev S, int n_nodes, cons
 }
 
 // Stand-alone local adjustment (bhmc_commit_move): paths by descent from the root.
-__global__ void __launch_bounds__(128) k_commit(SysDev S, int i, double bx, double by, double bz, int* status) {
+__global__ void __launch_bounds__(256) k_commit(SysDev S, int i, double bx, double by, double bz, int* status) {
   __shared__ MoveStore st;
   MoveSh& sh = st.sh;
   init_tables(sh, S.K);
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(128) k_commit(SysDev S, int i, double bx, doub
     sh.b[2] = bz;
   }
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
+  if (threadIdx.x < 4) sh.leafcnt[threadIdx.x] = -1;
   __syncthreads();
   setup_move(S, sh);
   __syncthreads();

@@ -9,7 +9,8 @@
 
 #define BHMC_MAX_P 6
 #define BHMC_MAX_D 20
-#define BHMC_MAX_WARPS 4
+#define BHMC_MAX_WARPS 8
+#define BHMC_ENERGY_WARPS 4
 #define BHMC_STACK 768          // traversal stack entries per warp
 #define BHMC_MAX_C 32
 

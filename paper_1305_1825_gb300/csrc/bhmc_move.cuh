@@ -3,7 +3,7 @@
 // positions of the ion and its image (Sec. 1, Sec. 3.2), acceptance (Sec. 2)
 // and the local adjustment of the octree (Sec. 3.3) with split/merge.
 //
-// A move is executed by one thread block (1, 2 or 4 warps).  Serial control
+// A move is executed by one thread block (1, 2, 4 or 8 warps).  Serial control
 // decisions are taken by thread 0; every loop over points, levels, moment
 // terms or leaf slots is spread over the lanes.
 #pragma once
@@ -119,12 +119,21 @@ static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
       T.x[s][k] = pts[s][k];
       T.hi[s][k] = f.x;
       T.lo[s][k] = f.y;
+      reinterpret_cast<float*>(&T.h4[s])[k] = f.x;
+      reinterpret_cast<float*>(&T.l4[s])[k] = f.y;
       if (s == 0 || s == 2) {
         T.ex[s >> 1][k] = pts[s][k];
         T.ehi[s >> 1][k] = f.x;
         T.elo[s >> 1][k] = f.y;
       }
-    } else if (lane == 12) {
+    } else if (lane >= 12 && lane < 12 + 3 * (4 - sh.npts)) {
+      // unused points sit far outside the root so that they never touch a cluster
+      const int s = sh.npts + (lane - 12) / 3, k = (lane - 12) % 3;
+      reinterpret_cast<float*>(&T.h4[s])[k] = 3.0e38f;
+      reinterpret_cast<float*>(&T.l4[s])[k] = 0.0f;
+      T.pkey[s] = 0ULL;
+    }
+    if (lane == 31) {
       const double w[4] = {-sh.q, sh.q, -sh.qa_img, sh.qb_img};
       for (int s = 0; s < sh.npts; ++s) {
         T.w64[s] = w[s];
@@ -147,9 +156,11 @@ template <int P, typename Real, int LAYOUT>
 __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
   MoveSh& sh = st.sh;
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
+  if (threadIdx.x < 4) sh.leafcnt[threadIdx.x] = -1;
   __syncthreads();
   TravOut o;
-  block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr, o);
+  block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr,
+                                  sh.leafcnt, o);
   if (threadIdx.x == 0) {
     double s = o.sum;
     sh.cnt[0][0] = o.visited;
@@ -186,13 +197,18 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
 }
 
 // Complete the cluster paths of the points by descending from the deepest
-// recorded cluster, and read the path leaves' counts (threads 0..npts-1).
+// recorded cluster, and read the path leaves' counts (threads 0..npts-1).  A
+// path the traversal followed down to its leaf needs no memory access.
 static __device__ void complete_paths(const SysDev& S, MoveSh& sh) {
   const int s = threadIdx.x;
   if (s < sh.npts) {
     int d = 0;
     if (sh.path[s][0] < 0) sh.path[s][0] = 0;
     while (d < S.Dmax && sh.path[s][d + 1] >= 0) ++d;
+    if (sh.leafcnt[s] >= 0) {
+      sh.plen[s] = d;
+      return;
+    }
     int node = sh.path[s][d];
     int4 b = S.nB[node];
     while (b.x >= 0 && d < S.Dmax) {
@@ -441,8 +457,22 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
     }
   }
   __syncthreads();
-  // (D) split the new leaves while they hold more than C charges
-  for (int m = 0; m < sh.nmov; ++m) {
+  // (D) split the new leaves while they hold more than C charges.  Without a
+  // merge the new leaves' counts follow from the pre-move counts.
+  bool may_split = true;
+  if (sh.merge_d[0] >= NL && (sh.nmov < 2 || sh.merge_d[1] >= NL)) {
+    may_split = false;
+    for (int m = 0; m < sh.nmov; ++m) {
+      const int L = sh.path[2 * m + 1][sh.plen[2 * m + 1]];
+      int c = sh.leafcnt[2 * m + 1];
+      for (int u = 0; u < sh.nmov; ++u) {
+        const int ua = sh.path[2 * u][sh.plen[2 * u]], ub = sh.path[2 * u + 1][sh.plen[2 * u + 1]];
+        if (ua != ub) c += (ub == L) - (ua == L);
+      }
+      if (c > S.C) may_split = true;
+    }
+  }
+  for (int m = 0; m < sh.nmov && may_split; ++m) {
     const int j = m ? sh.img : sh.i;
     for (int guard = 0; guard <= BHMC_MAX_D; ++guard) {
       if (tid == 0) {
@@ -617,7 +647,7 @@ struct DeltaOut {
 };
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(128) k_delta(SysDev S, int i, double bx, double by, double bz,
+__global__ void __launch_bounds__(256) k_delta(SysDev S, int i, double bx, double by, double bz,
                                                DeltaOut* out) {
   __shared__ MoveStore st;
   if (threadIdx.x == 0) {
@@ -643,7 +673,7 @@ __global__ void __launch_bounds__(128) k_delta(SysDev S, int i, double bx, doubl
 }
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(128) k_step(SysDev S, unsigned long long m, unsigned replica,
+__global__ void __launch_bounds__(256) k_step(SysDev S, unsigned long long m, unsigned replica,
                                               uint2 key, double step, MoveRec* recs,
                                               bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
@@ -663,7 +693,7 @@ struct BatchArgs {
 };
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(128) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
+__global__ void __launch_bounds__(256) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
                                                int* next, bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   __shared__ int rep;
@@ -698,9 +728,9 @@ __global__ void __launch_bounds__(128) k_batch(const SysDev* views, int n_rep, c
 
 // Full treecode energy: one warp per target charge j, S = {j}.
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(128) k_energy(SysDev S, double* partial, int* err) {
-  __shared__ TravPts Tw[BHMC_MAX_WARPS];
-  __shared__ WarpStore ws[BHMC_MAX_WARPS];
+__global__ void __launch_bounds__(32 * BHMC_ENERGY_WARPS) k_energy(SysDev S, double* partial, int* err) {
+  __shared__ TravPts Tw[BHMC_ENERGY_WARPS];
+  __shared__ WarpStore ws[BHMC_ENERGY_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int W = blockDim.x >> 5;
   double acc = 0.0;

@@ -30,6 +30,7 @@ struct TravPts {
   double ex[2][3];
   float ehi[2][3], elo[2][3];  // excluded positions as float pairs
   float eqf[2];
+  float4 h4[4], l4[4];         // the points' float pairs as vectors (w unused)
 };
 
 struct WarpStore {
