@@ -38,7 +38,8 @@ typedef enum {
   BHMC_ETIMEOUT = 7,    /* a bounded device loop ran out of iterations */
   BHMC_ESTATE = 8,      /* the context holds an earlier device error */
   BHMC_ECAPACITY = 9,   /* a depth-Dmax cell would hold more than C charges */
-  BHMC_ESTACK = 10      /* a traversal stack overflowed */
+  BHMC_ESTACK = 10,     /* a traversal stack overflowed */
+  BHMC_ESCRATCH = 11    /* problem larger than a call's fixed scratch allows */
 } bhmc_status;
 
 enum { BHMC_PREC_F32 = 0, BHMC_PREC_F64 = 1 };   /* traversal arithmetic */
@@ -162,6 +163,21 @@ bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E);
    the number of rows written.  EINVAL if a buffer is too small. */
 bhmc_status bhmc_export_tree(bhmc_ctx* ctx, int64_t* rows, int64_t max_rows, int64_t* members,
                              int64_t max_members, double* moments, int64_t* n_rows);
+
+/* Direct-sum total energy E = (1/2) l_B sum_{i != j} q_i q_j / r_ij (FP64) of
+   n charges, for callers that must not allocate device memory: code running
+   during stream capture, host functions enqueued on a stream, or hosts that
+   own all device memory.  The paper has no counterpart; it is the variant of
+   bhmc_energy_direct whose scratch is a fixed 32 KiB array inside the library.
+   q[n], xyz[3n] (x,y,z interleaved) and E[1] are DEVICE pointers; E is written
+   on cuda_stream (no host synchronisation).  n <= 1048576, else BHMC_ESCRATCH.
+   No allocation of any kind happens.  The first call on a device looks up the
+   scratch's device address for that device; make it before capturing a stream.
+   All calls share the scratch, so calls whose kernels overlap on one device
+   race; each call writes every scratch entry it reads, so nothing needs
+   clearing between calls. */
+bhmc_status bhmc_energy_direct_noalloc(int64_t n, const double* q, const double* xyz, double lB,
+                                       double* E, void* cuda_stream);
 
 /* ---- batches of independent replicas (one octree each) ---- */
 

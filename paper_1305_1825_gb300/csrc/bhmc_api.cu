@@ -79,6 +79,7 @@ const char* bhmc_status_string(bhmc_status s) {
     case BHMC_ESTATE: return "context holds an earlier device error";
     case BHMC_ECAPACITY: return "depth-Dmax cell over capacity";
     case BHMC_ESTACK: return "traversal stack overflow";
+    case BHMC_ESCRATCH: return "problem larger than the call's fixed scratch";
   }
   return "unknown status";
 }
