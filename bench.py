@@ -53,6 +53,22 @@ def dist_env():
     return rank, world, local
 
 
+def traffic_record():
+    """DRAM bytes per trial move of the batched kernel from the committed ncu
+    capture, if the kernel sources are unchanged since that capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_batch_traffic.json")))
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_1305_1825_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() == rec["sources_sha256"]:
+            return rec
+    except Exception:
+        pass
+    return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
@@ -293,8 +309,12 @@ def run_gpu(args):
     bpm, detail = algorithmic_bytes_per_move(bhmc, batch, systems, K, acc_rate)
     launch_ms = ms / args.steps
     achieved = bpm * args.reps * args.moves / (launch_ms / 1e3) / 1e9
+    trec = traffic_record()
+    traffic = trec["dram_bytes_per_move"] * args.reps * args.moves if trec else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_src,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "peak_source": pk_src,
+            "traffic_note": ("ncu dram bytes per move of a 96-replica capture x moves per launch"
+                             if trec else "kernel changed since the last ncu capture"),
             "kernel": "k_batch (persistent, one replica per block)",
             "bytes_per_move": bpm, "per_move": detail}
     extra = {}

@@ -290,6 +290,8 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
   }
   int groups = 1;
   int* dcount = dflags + 4;
+  // level d holds nodes [level_begin[d], level_begin[d + 1]); the root level is node 0
+  std::vector<int> level_begin{0, 1};
   for (int depth = 0; n_list > 0; ++depth) {
     if (groups + n_list > S.group_cap) {
       cleanup();
@@ -300,7 +302,9 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
       cleanup();
       return BHMC_ECUDA;
     }
+    level_begin.back() = 8 * groups;
     groups += n_list;
+    level_begin.push_back(8 * groups);
     if (cudaMemcpyAsync(&n_list, dcount, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       cleanup();
@@ -309,7 +313,7 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
     std::swap(la, lb);
   }
   if (cudaMemcpyAsync(S.pool, &groups, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      build_leaves_moments(S, 8 * groups, perm, seg, dflags, st) != cudaSuccess ||
+      build_leaves_moments(S, 8 * groups, perm, seg, dflags, level_begin.data(), (int)level_begin.size(), st) != cudaSuccess ||
       cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cleanup();

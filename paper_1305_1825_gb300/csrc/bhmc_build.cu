@@ -178,17 +178,15 @@ __global__ void k_fill_leaves(SysDev S, int n_nodes, const int* perm, const int*
   }
 }
 
-// M_A^n = sum_{j in A} q_j (r_j - r_A)^n in FP64.  Small clusters: one thread
-// per (cluster, term), members in index order.  Large clusters: one block per
-// cluster and term-by-term block reductions.
-__global__ void k_moments_small(SysDev S, int n_nodes, const int* perm, const int* seg, int big) {
+// Leaf moments M_A^n = sum_{j in A} q_j (r_j - r_A)^n (Eq. 3.3) in FP64, one
+// thread per (leaf, term), members in index order.
+__global__ void k_moments_leaves(SysDev S, int n_nodes, const int* perm, const int* seg) {
   const long long total = (long long)n_nodes * S.K;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
        it += (long long)gridDim.x * blockDim.x) {
     const int nd = (int)(it / S.K), t = (int)(it - (long long)nd * S.K);
     const int4 b = S.nB[nd];
-    if (b.z == 0 && b.w == 0) continue;
-    if (b.y > big) continue;
+    if ((b.z == 0 && b.w == 0) || b.x >= 0) continue;
     const float4 c = S.nA[nd];
     int n1, n2, n3;
     term_exponents(t, n1, n2, n3);
@@ -203,33 +201,45 @@ __global__ void k_moments_small(SysDev S, int n_nodes, const int* perm, const in
   }
 }
 
-__global__ void __launch_bounds__(256) k_moments_big(SysDev S, int n_nodes, const int* perm, const int* seg,
-                                                     int big) {
-  __shared__ double red[8];
-  for (int nd = blockIdx.x; nd < n_nodes; nd += gridDim.x) {
+// Internal clusters of one level from their eight children (moments shifted
+// from the child centre to the parent centre, both exact dyadic points):
+// M_P^n = sum_children sum_{m <= n} C(n, m) d^(n - m) M_child^m, d = r_child - r_P.
+__global__ void k_moments_m2m(SysDev S, int node_begin, int node_end) {
+  const long long total = (long long)(node_end - node_begin) * S.K;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int nd = node_begin + (int)(it / S.K), t = (int)(it % S.K);
     const int4 b = S.nB[nd];
-    if ((b.z == 0 && b.w == 0) || b.y <= big) continue;
+    if ((b.z == 0 && b.w == 0) || b.x < 0) continue;
     const float4 c = S.nA[nd];
-    for (int t = 0; t < S.K; ++t) {
-      int n1, n2, n3;
-      term_exponents(t, n1, n2, n3);
-      double M = 0.0;
-      for (int k = threadIdx.x; k < b.y; k += blockDim.x) {
-        const int j = perm[seg[nd] + k];
-        M += mono_term(n1, n2, n3, S.pq[j], __dsub_rn(S.px[j], (double)c.x), __dsub_rn(S.py[j], (double)c.y),
-                       __dsub_rn(S.pz[j], (double)c.z));
+    int n1, n2, n3;
+    term_exponents(t, n1, n2, n3);
+    double M = 0.0;
+    for (int o = 0; o < 8; ++o) {
+      const int ch = b.x + o;
+      const float4 cc = S.nA[ch];
+      const double d[3] = {(double)cc.x - (double)c.x, (double)cc.y - (double)c.y, (double)cc.z - (double)c.z};
+      const double* Mc = S.M64 + (size_t)ch * S.K;
+      double b1 = 1.0;  // C(n1, m1) d1^(n1 - m1), m1 from n1 down to 0
+      double p1 = 1.0;
+      for (int m1 = n1; m1 >= 0; --m1) {
+        double p2 = 1.0, b2 = 1.0;
+        for (int m2 = n2; m2 >= 0; --m2) {
+          double p3 = 1.0, b3 = 1.0;
+          for (int m3 = n3; m3 >= 0; --m3) {
+            M += (b1 * p1) * (b2 * p2) * (b3 * p3) * Mc[tidx(m1, m2, m3)];
+            p3 *= d[2];
+            b3 = b3 * (double)m3 / (double)(n3 - m3 + 1);
+          }
+          p2 *= d[1];
+          b2 = b2 * (double)m2 / (double)(n2 - m2 + 1);
+        }
+        p1 *= d[0];
+        b1 = b1 * (double)m1 / (double)(n1 - m1 + 1);
       }
-      for (int o = 16; o > 0; o >>= 1) M += __shfl_xor_sync(0xffffffffu, M, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = M;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        S.M64[(size_t)nd * S.K + t] = s;
-        if (S.prec == BHMC_PREC_F32) S.M32[m32_index(S, nd, t)] = __double2float_rn(s);
-      }
-      __syncthreads();
     }
+    S.M64[(size_t)nd * S.K + t] = M;
+    if (S.prec == BHMC_PREC_F32) S.M32[m32_index(S, nd, t)] = __double2float_rn(M);
   }
 }
 
@@ -334,11 +344,14 @@ cudaError_t build_compact(const int* in, int n, int* out, int* n_out, cudaStream
   return cudaGetLastError();
 }
 cudaError_t build_leaves_moments(const SysDev& S, int n_nodes, const int* perm, const int* seg, int* flags,
-                                 cudaStream_t st) {
+                                 const int* level_begin, int n_levels, cudaStream_t st) {
   k_fill_leaves<<<grid_for(n_nodes, 256), 256, 0, st>>>(S, n_nodes, perm, seg, flags);
-  const int big = 64;
-  k_moments_small<<<grid_for((long long)n_nodes * S.K, 256), 256, 0, st>>>(S, n_nodes, perm, seg, big);
-  k_moments_big<<<n_nodes < 4096 ? n_nodes : 4096, 256, 0, st>>>(S, n_nodes, perm, seg, big);
+  k_moments_leaves<<<grid_for((long long)n_nodes * S.K, 256), 256, 0, st>>>(S, n_nodes, perm, seg);
+  // internal clusters bottom-up: level d occupies nodes [level_begin[d], level_begin[d + 1])
+  for (int d = n_levels - 2; d >= 0; --d) {
+    const int b = level_begin[d], e = level_begin[d + 1];
+    k_moments_m2m<<<grid_for((long long)(e - b) * S.K, 256), 256, 0, st>>>(S, b, e);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st) {
