@@ -808,6 +808,7 @@ int or_mc_run(or_sys* s, uint64_t seed, uint32_t replica, uint64_t m0, int64_t n
               double step, or_record* recs, int64_t* n_accepted) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   int64_t acc = 0;
+  if (n_moves > 0 && s->n_mob < 1) return OR_EINVAL; /* no mobile ion to move */
   for (int64_t t = 0; t < n_moves; ++t) {
     uint64_t mm = m0 + (uint64_t)t;
     uint32_t ctr[4] = {(uint32_t)mm, (uint32_t)(mm >> 32), replica, 0u};

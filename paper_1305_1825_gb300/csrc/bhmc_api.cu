@@ -480,6 +480,7 @@ bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t 
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
   if (!stats || !(step >= 0.0)) return BHMC_EINVAL;
+  if (n_moves > 0 && ctx->S.n_mob < 1) return BHMC_EINVAL;  // no mobile ion to move
   IoBlock* dio = static_cast<IoBlock*>(ctx->io);
   IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
   MoveRec* drec = nullptr;
@@ -746,8 +747,10 @@ bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, con
                                uint64_t move0, bhmc_mc_stats* stats) {
   if (!B || !seeds || !(step >= 0.0)) return BHMC_EINVAL;
   const int n = (int)B->reps.size();
-  for (bhmc_ctx* c : B->reps)
+  for (bhmc_ctx* c : B->reps) {
     if (c->sticky) return BHMC_ESTATE;
+    if (n_moves > 0 && c->S.n_mob < 1) return BHMC_EINVAL;  // no mobile ion to move
+  }
   CK(cudaMemcpyAsync(B->d_seeds, seeds, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, B->stream));
   CK(cudaStreamSynchronize(B->stream));
   B->h_args->n_moves = n_moves;

@@ -91,14 +91,16 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
   return v;
 }
 
-// Returns 0 if the point is outside the root cube.
+// Returns 0 if the point is outside the root cube (NaN and infinities included:
+// the range test is done on the floored doubles before any integer conversion).
 __device__ __forceinline__ unsigned long long point_key(const SysDev& S, double x, double y,
                                                         double z) {
-  long long lim = 1LL << S.Dmax;
-  long long kx = (long long)floor(__dmul_rn(x, S.inv_hmin)) - S.root_cell[0];
-  long long ky = (long long)floor(__dmul_rn(y, S.inv_hmin)) - S.root_cell[1];
-  long long kz = (long long)floor(__dmul_rn(z, S.inv_hmin)) - S.root_cell[2];
-  if (kx < 0 || ky < 0 || kz < 0 || kx >= lim || ky >= lim || kz >= lim) return 0ULL;
+  const double lim = (double)(1LL << S.Dmax);
+  const double fx = floor(__dmul_rn(x, S.inv_hmin)) - (double)S.root_cell[0];
+  const double fy = floor(__dmul_rn(y, S.inv_hmin)) - (double)S.root_cell[1];
+  const double fz = floor(__dmul_rn(z, S.inv_hmin)) - (double)S.root_cell[2];
+  if (!(fx >= 0.0 && fx < lim && fy >= 0.0 && fy < lim && fz >= 0.0 && fz < lim)) return 0ULL;
+  const long long kx = (long long)fx, ky = (long long)fy, kz = (long long)fz;
   return (1ULL << (3 * S.Dmax)) | spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
 }
 
