@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--moves", type=int, default=2000, help="trial moves per replica per step")
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--p", type=int, default=4)
-    ap.add_argument("--C", type=int, default=8)
+    ap.add_argument("--C", type=int, default=16, help="leaf capacity (autotuned: profiles/autotune_colloid64.md)")
     ap.add_argument("--warps", type=int, default=8)
     ap.add_argument("--layout", default="aos", choices=["soa", "aos"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -81,9 +81,10 @@ def test_colloid_1e4_chain(bh, oracle_mod):
     assert ctx.export_tree() == ref.export_tree()
 
 
-def test_batch_256_replicas_sampled(bh, oracle_mod):
+@pytest.mark.parametrize("C", [8, 16])
+def test_batch_256_replicas_sampled(bh, oracle_mod, C):
     sizes = W.batch_sizes(256, seed=3)
-    systems = W.batch(sizes=sizes)
+    systems = W.batch(sizes=sizes, C=C)
     batch = bh.Batch(systems, **BENCH)
     seeds = [1000 + r for r in range(256)]
     stats = batch.step_mc(150, 1.0, seeds)
