@@ -153,6 +153,10 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);
 /* Total treecode energy E = (1/2) l_B sum_i q_i phi_tree(r_i), every charge
    excluded from its own sum (Eq. 1.1 evaluated by the Sec. 3.2 traversal). */
 bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E);
+/* Treecode potential of every charge, phi_j = sum over the tree minus j of
+   q_k / |r_k - r_j| (the traversal of Sec. 3.2 at r_j), into phi[n_charges]
+   (host or device memory per flags).  The same pass as bhmc_energy. */
+bhmc_status bhmc_potentials(bhmc_ctx* ctx, double* phi, int32_t flags);
 /* Total energy by direct O(N^2) summation of Eq. (1.1) on the GPU (FP64). */
 bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E);
 

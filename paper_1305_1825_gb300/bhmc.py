@@ -87,6 +87,7 @@ def lib():
         L.bhmc_set_energy.argtypes = [C.c_void_p, C.c_double]
         L.bhmc_energy.argtypes = [C.c_void_p, _dp]
         L.bhmc_energy_direct.argtypes = [C.c_void_p, _dp]
+        L.bhmc_potentials.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
         L.bhmc_export_tree.argtypes = [C.c_void_p, _i64p, C.c_int64, _i64p, C.c_int64, _dp, _i64p]
         L.bhmc_batch_create.argtypes = [C.c_int32, C.POINTER(Params), _i64p, _i64p,
                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
@@ -208,6 +209,12 @@ def bhmc_energy_direct(h):
     e = C.c_double()
     _check(lib().bhmc_energy_direct(h, C.byref(e)), "bhmc_energy_direct")
     return e.value
+
+
+def bhmc_potentials(h):
+    phi = np.zeros(bhmc_n_charges(h))
+    _check(lib().bhmc_potentials(h, C.c_void_p(phi.ctypes.data), HOST_PTRS), "bhmc_potentials")
+    return phi
 
 
 def bhmc_get_energy(h):
@@ -339,6 +346,9 @@ class Context:
 
     def energy_direct(self):
         return bhmc_energy_direct(self.h)
+
+    def potentials(self):
+        return bhmc_potentials(self.h)
 
     def get_energy(self):
         return bhmc_get_energy(self.h)

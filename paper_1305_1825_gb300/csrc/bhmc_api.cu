@@ -125,6 +125,7 @@ static size_t arena_bytes(const SysDev& S) {
   add(4 * sizeof(double) * S.n_tot);  // px py pz pq
   add(sizeof(unsigned long long) * S.n_tot);
   add(2 * sizeof(int) * S.n_tot);
+  add(sizeof(int) * S.n_tot);
   add(sizeof(float4) * S.node_cap);
   add(sizeof(int4) * S.node_cap);
   add(sizeof(float) * (size_t)S.node_cap * S.Kp);
@@ -146,6 +147,7 @@ static void carve_all(SysDev& S, char* base) {
   S.ckey = carve<unsigned long long>(cur, S.n_tot);
   S.leaf_of = carve<int>(cur, S.n_tot);
   S.slot_of = carve<int>(cur, S.n_tot);
+  S.order = carve<int>(cur, S.n_tot);
   S.nA = carve<float4>(cur, S.node_cap);
   S.nB = carve<int4>(cur, S.node_cap);
   S.M32 = carve<float>(cur, (size_t)S.node_cap * S.Kp);
@@ -313,6 +315,7 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
     std::swap(la, lb);
   }
   if (cudaMemcpyAsync(S.pool, &groups, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(S.order, perm, sizeof(int) * S.n_tot, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       build_leaves_moments(S, 8 * groups, perm, seg, dflags, level_begin.data(), (int)level_begin.size(), st) != cudaSuccess ||
       cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
@@ -523,21 +526,20 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E) {
   return BHMC_OK;
 }
 
-static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, int* err) {
+static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, double* phi, int* err) {
   const int w = BHMC_ENERGY_WARPS;
   switch (c->P.p) {
-    case 2: return launch_energy<2>(c->S, w, grid, partial, err, c->stream);
-    case 4: return launch_energy<4>(c->S, w, grid, partial, err, c->stream);
-    default: return launch_energy<6>(c->S, w, grid, partial, err, c->stream);
+    case 2: return launch_energy<2>(c->S, w, grid, partial, phi, err, c->stream);
+    case 4: return launch_energy<4>(c->S, w, grid, partial, phi, err, c->stream);
+    default: return launch_energy<6>(c->S, w, grid, partial, phi, err, c->stream);
   }
 }
 
-bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {
+static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_t flags) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
-  if (!E) return BHMC_EINVAL;
-  const int warps = BHMC_ENERGY_WARPS;
-  int grid = (ctx->S.n_tot + warps - 1) / warps;
+  const int warps = BHMC_ENERGY_WARPS;  // each warp evaluates 32 targets at a time
+  int grid = (ctx->S.n_tot + 32 * warps - 1) / (32 * warps);
   grid = std::min(grid, 152 * 16);
   double* partial = nullptr;
   int* derr = nullptr;
@@ -546,22 +548,46 @@ bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {
     cudaFree(partial);
     return BHMC_ENOMEM;
   }
+  double* dphi = nullptr;
+  if (phi_out) {
+    if (flags & BHMC_DEVICE_PTRS) {
+      dphi = phi_out;
+    } else if (cudaMalloc(&dphi, sizeof(double) * ctx->S.n_tot) != cudaSuccess) {
+      cudaFree(partial);
+      cudaFree(derr);
+      return BHMC_ENOMEM;
+    }
+  }
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
   bool ok = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream) == cudaSuccess &&
-            dispatch_energy(ctx, grid, partial, derr) == cudaSuccess &&
+            dispatch_energy(ctx, grid, partial, dphi, derr) == cudaSuccess &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                             ctx->stream) == cudaSuccess &&
-            cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
-            cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+            cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess;
+  if (ok && phi_out && !(flags & BHMC_DEVICE_PTRS))
+    ok = cudaMemcpyAsync(phi_out, dphi, sizeof(double) * ctx->S.n_tot, cudaMemcpyDeviceToHost, ctx->stream) ==
+         cudaSuccess;
+  ok = ok && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
   cudaFree(partial);
   cudaFree(derr);
+  if (phi_out && !(flags & BHMC_DEVICE_PTRS)) cudaFree(dphi);
   if (!ok) return BHMC_ECUDA;
   if (herr) return (bhmc_status)herr;
   double s = 0.0;
   for (double v : h) s += v;
-  *E = 0.5 * ctx->S.lB * s;
+  if (E) *E = 0.5 * ctx->S.lB * s;
   return BHMC_OK;
+}
+
+bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {
+  if (!E) return BHMC_EINVAL;
+  return energy_impl(ctx, E, nullptr, 0);
+}
+
+bhmc_status bhmc_potentials(bhmc_ctx* ctx, double* phi, int32_t flags) {
+  if (!phi) return BHMC_EINVAL;
+  return energy_impl(ctx, nullptr, phi, flags);
 }
 
 bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E) {

@@ -11,7 +11,6 @@
 #define BHMC_MAX_D 20
 #define BHMC_MAX_WARPS 8
 #define BHMC_ENERGY_WARPS 4
-#define BHMC_STACK 768          // traversal stack entries per warp
 #define BHMC_MAX_C 32
 
 namespace bhmc {
@@ -46,6 +45,7 @@ struct SysDev {
   unsigned long long* ckey;
   int* leaf_of;
   int* slot_of;
+  int* order;   // charges in the Morton order of the build (spatially coherent targets)
   // nodes
   int node_cap, group_cap;
   float4* nA;

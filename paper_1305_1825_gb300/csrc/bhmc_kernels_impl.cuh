@@ -4,6 +4,7 @@
 
 #include "bhmc_launch.cuh"
 #include "bhmc_move.cuh"
+#include "bhmc_energy.cuh"
 
 namespace bhmc {
 
@@ -60,14 +61,14 @@ int batch_occupancy<BHMC_P>(const SysDev& S0, int warps) {
 }
 
 template <>
-cudaError_t launch_energy<BHMC_P>(const SysDev& S, int warps, int grid, double* partial, int* err,
-                                  cudaStream_t st) {
+cudaError_t launch_energy<BHMC_P>(const SysDev& S, int warps, int grid, double* partial, double* phi,
+                                  int* err, cudaStream_t st) {
   if (S.prec == BHMC_PREC_F64)
-    k_energy<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+    k_energy<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
   else if (S.layout == BHMC_LAYOUT_AOS)
-    k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+    k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
   else
-    k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, partial, err);
+    k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ cudaError_t launch_batch(const SysDev& S0, int warps, const SysDev* views, int n
 template <int P>
 int batch_occupancy(const SysDev& S0, int warps);
 template <int P>
-cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial, int* err,
+cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial, double* phi, int* err,
                           cudaStream_t st);
 
 #define BHMC_EXTERN_P(P)                                                                         \
@@ -36,7 +36,7 @@ cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial,
                                               const BatchArgs*, int*, bhmc_mc_stats*,            \
                                               cudaStream_t);                                     \
   template <> int batch_occupancy<P>(const SysDev&, int);                                    \
-  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, int*, cudaStream_t);
+  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, cudaStream_t);
 
 BHMC_EXTERN_P(2)
 BHMC_EXTERN_P(4)

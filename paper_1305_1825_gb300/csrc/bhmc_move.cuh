@@ -726,43 +726,4 @@ __global__ void __launch_bounds__(256) k_batch(const SysDev* views, int n_rep, c
   }
 }
 
-// Full treecode energy: one warp per target charge j, S = {j}.
-template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(32 * BHMC_ENERGY_WARPS) k_energy(SysDev S, double* partial, int* err) {
-  __shared__ TravPts Tw[BHMC_ENERGY_WARPS];
-  __shared__ WarpStore ws[BHMC_ENERGY_WARPS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int W = blockDim.x >> 5;
-  double acc = 0.0;
-  for (int j = blockIdx.x * W + warp; j < S.n_tot; j += gridDim.x * W) {
-    TravPts& T = Tw[warp];
-    if (lane < 3) {
-      const double x = lane == 0 ? S.px[j] : (lane == 1 ? S.py[j] : S.pz[j]);
-      const float2 f = split2(x);
-      T.x[0][lane] = x;
-      T.hi[0][lane] = f.x;
-      T.lo[0][lane] = f.y;
-      T.ex[0][lane] = x;
-      T.ehi[0][lane] = f.x;
-      T.elo[0][lane] = f.y;
-    } else if (lane == 3) {
-      T.w[0] = 1.0f;
-      T.w64[0] = 1.0;
-      T.pkey[0] = 0ULL;
-      T.n_excl = 1;
-      T.excl[0] = j;
-      T.ekey[0] = S.ckey[j];
-      T.eq[0] = S.pq[j];
-      T.eqf[0] = (float)S.pq[j];
-    }
-    __syncwarp();
-    TravOut o;
-    warp_traverse<P, Real, LAYOUT>(S, T, ws[warp], 1u, nullptr, o);
-    if (o.err && lane == 0) atomicCAS(err, 0, o.err);
-    acc += S.pq[j] * o.sum;
-    __syncwarp();
-  }
-  if (lane == 0) partial[blockIdx.x * W + warp] = acc;
-}
-
 }  // namespace bhmc

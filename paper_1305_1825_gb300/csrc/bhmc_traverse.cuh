@@ -1,15 +1,14 @@
-// bhmc_traverse.cuh -- warp-cooperative octree traversal (Sec. 3.2) evaluating
-// the potential of the tree minus an excluded set at up to four points at once.
+// bhmc_traverse.cuh -- building blocks of the octree traversal (Sec. 3.2):
+// the evaluation points, the MAC, the multipole term of a cluster with the
+// excluded charges removed, direct leaf terms and compensated accumulation.
 //
-// Each lane examines one cluster; a round pops up to four groups of eight
-// siblings from a per-warp stack in shared memory.  A stack entry carries two
-// 4-bit masks over the evaluation points: `open` (regular traversal: MAC test,
-// then multipole / open / direct) and `forced` (inside a cluster that failed the
-// MAC with N'_A <= N_0: direct over all its particles, no MAC).  The MAC
-// decision of every (cluster, point) pair is the FP64 decision
+// The MAC decision of every (cluster, point) pair is the FP64 decision
 // rho_A^2 <= theta^2 ((dx*dx + dy*dy) + dz*dz): FP32 settles it when the value
 // is further than 2^-17 (relative) from the threshold, the exact FP64 sequence
-// otherwise.
+// otherwise.  Error analysis: with x = hi + lo (hi = fl(x), lo = fl(x - hi)) and
+// an exact FP32 centre c, R = (c - hi) - lo has |R - (c - x)| <= 2u|c - x| +
+// 2u^2|x| (u = 2^-24); theta^2 |R|^2 in FP32 is then within about 10u relative of
+// the exact value, well inside the 2^-17 band.
 #pragma once
 
 #include "bhmc_common.cuh"
@@ -31,12 +30,6 @@ struct TravPts {
   float ehi[2][3], elo[2][3];  // excluded positions as float pairs
   float eqf[2];
   float4 h4[4], l4[4];         // the points' float pairs as vectors (w unused)
-};
-
-struct WarpStore {
-  uint2 stk[BHMC_STACK];
-  unsigned mi[128];        // multipole items: node << 4 | excluded-inside mask << 2 | point
-  uint2 di[32];            // direct items: {leaf, count << 4 | point mask}
 };
 
 struct TravOut {
@@ -215,174 +208,6 @@ __device__ __forceinline__ void direct_slot(const SysDev& S, const TravPts& T, f
     }
     ++pairs;
   }
-}
-
-// Traverse from the root for the points in `pmask`; `path` (may be null)
-// receives, per point and level, the cluster containing the point.  The
-// headers of the next round's clusters are loaded before the current round's
-// multipole and direct terms are evaluated, so their latency overlaps compute.
-template <int P, typename Real, int LAYOUT>
-__device__ void warp_traverse(const SysDev& S, const TravPts& T, WarpStore& W, unsigned pmask,
-                              int (*path)[BHMC_MAX_D + 1], TravOut& out) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 3;
-  Acc<Real> acc;
-  int visited = 0, accepted = 0, pairs = 0, fp64 = 0, err = 0;
-  int cp = 1;
-  while (cp < S.C) cp <<= 1;
-  const int lg = 31 - __clz(cp);
-  const int SC = S.C + 2;
-  // first round: the root group {root, 7 empty slots}
-  int top = 0;
-  int npop = 1;
-  uint2 e = make_uint2(0u, g == 0 ? pmask : 0u);
-  int4 b = make_int4(-1, 0, 0, 0);
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (g == 0) {
-    b = S.nB[lane & 7];
-    a = S.nA[lane & 7];
-  }
-  int rounds = 0;
-  while (npop > 0) {
-    if (++rounds > (1 << 22)) {
-      err = BHMC_ETIMEOUT;
-      break;
-    }
-    const int node = (int)e.x + (lane & 7);
-    const unsigned om = e.y & 15u, fd = (e.y >> 4) & 15u;
-    unsigned mac = 0, open = 0, fdc = 0, dir = 0, emask = 0;
-    int fc = -1, cnt = 0;
-    const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-    if (g < npop && (om | fd) && key != 0ULL) {
-      fc = b.x;
-      cnt = b.y;
-      const int d = key_depth(key);
-      const int sh = 3 * (S.Dmax - d);
-      for (int k = 0; k < T.n_excl; ++k) emask |= ((T.ekey[k] >> sh) == key) ? (1u << k) : 0u;
-      if (path) {
-        unsigned all = om | fd;
-        while (all) {
-          const int s = __ffs(all) - 1;
-          all &= all - 1;
-          if ((T.pkey[s] >> sh) == key) path[s][d] = node;
-        }
-      }
-      visited += __popc(om);
-      const int np = cnt - __popc(emask);
-      if (np > 0) {
-        unsigned m = om;
-        while (m) {
-          const int s = __ffs(m) - 1;
-          m &= m - 1;
-          const unsigned bit = 1u << s;
-          if (np >= S.N0 && mac_test<Real>(S, a, T, s, fp64))
-            mac |= bit;
-          else if (fc >= 0)
-            (np > S.N0 ? open : fdc) |= bit;
-          else
-            dir |= bit;
-        }
-        if (fd) {
-          if (fc >= 0)
-            fdc |= fd;
-          else
-            dir |= fd;
-        }
-      }
-    }
-    // children to the stack (the popped entries' slots are reused)
-    const bool push = (open | fdc) != 0;
-    const unsigned pb = __ballot_sync(FULL, push);
-    const int npush = __popc(pb);
-    if (top + npush > BHMC_STACK) {
-      err = BHMC_ESTACK;
-      break;
-    }
-    if (push) W.stk[top + __popc(pb & lanemask_lt())] = make_uint2((unsigned)fc, open | (fdc << 4));
-    top += npush;
-    // multipole and direct items of this round
-    const int nm = __popc(mac);
-    int incl = nm;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    {
-      int pos = incl - nm;
-      unsigned m = mac;
-      while (m) {
-        const int s = __ffs(m) - 1;
-        m &= m - 1;
-        W.mi[pos++] = ((unsigned)node << 4) | (emask << 2) | (unsigned)s;
-      }
-    }
-    accepted += nm;
-    const unsigned db = __ballot_sync(FULL, dir != 0);
-    const int ndir = __popc(db);
-    if (dir) W.di[__popc(db & lanemask_lt())] = make_uint2((unsigned)node, ((unsigned)cnt << 4) | dir);
-    __syncwarp();
-    // next round: pop and prefetch its headers
-    const int npop_n = min(top, 4);
-    uint2 e_n = make_uint2(0u, 0u);
-    int4 b_n = make_int4(-1, 0, 0, 0);
-    float4 a_n = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g < npop_n) {
-      e_n = W.stk[top - 1 - g];
-      const int nn = (int)e_n.x + (lane & 7);
-      b_n = S.nB[nn];
-      a_n = S.nA[nn];
-    }
-    top -= npop_n;
-    // first direct pass: issue its loads before the multipole work
-    const int per = 32 >> lg;
-    const int kk = lane & (cp - 1);
-    uint2 di0 = make_uint2(0u, 0u);
-    float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
-    bool have0 = false;
-    if ((lane >> lg) < ndir) {
-      di0 = W.di[lane >> lg];
-      if (kk < (int)(di0.y >> 4)) {
-        const int slot = (int)di0.x * SC + kk;
-        sa0 = S.sA[slot];
-        sb0 = S.sB[slot];
-        have0 = true;
-      }
-    }
-    for (int k = lane; k < total; k += 32) {
-      const unsigned it = W.mi[k];
-      const int s = (int)(it & 3u);
-      const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
-      acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
-    }
-    if (have0) direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
-    for (int base = per; base < ndir; base += per) {
-      const int item = base + (lane >> lg);
-      if (item < ndir) {
-        const uint2 di = W.di[item];
-        if (kk < (int)(di.y >> 4)) {
-          const int slot = (int)di.x * SC + kk;
-          direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
-        }
-      }
-    }
-    __syncwarp();
-    e = e_n;
-    b = b_n;
-    a = a_n;
-    npop = npop_n;
-  }
-  double v = acc.value();
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  out.sum = v;
-  out.visited = __reduce_add_sync(FULL, visited);
-  out.accepted = __reduce_add_sync(FULL, accepted);
-  out.pairs = __reduce_add_sync(FULL, pairs);
-  out.fp64 = __reduce_add_sync(FULL, fp64);
-  out.err = __reduce_max_sync(FULL, err);
 }
 
 }  // namespace bhmc

@@ -111,3 +111,30 @@ def test_large_colloid_1e6(bh, oracle_mod):
     assert _compare_chain(rec, orec) == 60
     q, x = ctx.charges()
     assert np.array_equal(x, ref.charges()[1])
+
+
+def _check_potentials(ctx, ref, n, seed):
+    """Sampled per-charge treecode potentials phi_j (j excluded) against the oracle."""
+    phi = ctx.potentials()
+    q, x = ref.charges()
+    rng = np.random.default_rng(seed)
+    for j in rng.choice(len(q), n, replace=False):
+        e = ref.phi(x[j], excl=[int(j)])
+        assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
+    return phi, q
+
+
+def test_colloid_1e4_potentials_and_energy(bh, oracle_mod):
+    wl = W.colloid(n=10000, seed=2)
+    ctx = bh.Context(wl, **BENCH)
+    ref = _oracle(oracle_mod, wl)
+    phi, q = _check_potentials(ctx, ref, 200, seed=7)
+    assert ctx.energy() == pytest.approx(0.5 * float(q @ phi), rel=1e-12)
+
+
+@pytest.mark.slow
+def test_large_colloid_1e6_potentials(bh, oracle_mod):
+    wl = W.large()
+    ctx = bh.Context(wl, **BENCH)
+    ref = _oracle(oracle_mod, wl)
+    _check_potentials(ctx, ref, 40, seed=8)
