@@ -157,6 +157,13 @@ bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E);
    q_k / |r_k - r_j| (the traversal of Sec. 3.2 at r_j), into phi[n_charges]
    (host or device memory per flags).  The same pass as bhmc_energy. */
 bhmc_status bhmc_potentials(bhmc_ctx* ctx, double* phi, int32_t flags);
+/* Gradient of the total treecode energy with every MAC decision held fixed
+   (the adjoint of the Sec. 3.2 traversal and of the moments of Eq. 3.3):
+   dEdr[3k..3k+2] = dE/dr_k (forces are -dEdr), dEdq[k] = dE/dq_k for every
+   charge (ions, fixed charges and images as independent charges); host or
+   device buffers per flags.  Scratch of about (8 + 8K nodes/charge) doubles per
+   charge is allocated for the call. */
+bhmc_status bhmc_forces(bhmc_ctx* ctx, double* dEdr, double* dEdq, int32_t flags);
 /* Total energy by direct O(N^2) summation of Eq. (1.1) on the GPU (FP64). */
 bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E);
 

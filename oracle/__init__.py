@@ -108,6 +108,7 @@ def lib():
         L.or_energy_tree.argtypes = [C.c_void_p]
         L.or_energy_tree.restype = C.c_double
         L.or_potentials.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_forces.argtypes = [C.c_void_p, _dp, _dp]
         L.or_export_tree.argtypes = [C.c_void_p, _i64p, C.c_int64, _i64p, C.c_int64]
         L.or_export_tree.restype = C.c_int64
         L.or_check.argtypes = [C.c_void_p]
@@ -260,6 +261,15 @@ class System:
         vd = np.zeros(self.n_charges)
         lib().or_potentials(self._h, vt.ctypes.data_as(_dp), vd.ctypes.data_as(_dp))
         return vt, vd
+
+    def forces(self):
+        """(dE/dr (n x 3), dE/dq (n)) of the treecode energy, MAC decisions fixed."""
+        g = np.zeros((self.n_charges, 3))
+        dq = np.zeros(self.n_charges)
+        rc = lib().or_forces(self._h, g.ctypes.data_as(_dp), dq.ctypes.data_as(_dp))
+        if rc:
+            raise ValueError("or_forces failed with status %d" % rc)
+        return g, dq
 
     def export_tree(self):
         """{(depth, key): (is_leaf, count, members-tuple or None)}"""

@@ -989,3 +989,137 @@ int or_node_moments(const or_sys* s, int depth, uint64_t key, double* M) {
   }
   return OR_EINVAL;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Exact gradient of E_tree = (1/2) l_B sum_i q_i phi_i with every MAC decision
+   held fixed.  phi_i = sum over accepted clusters A of sum_n T_n(r_A - r_i) M_A^n
+   + sum over direct partners j of q_j/|r_j - r_i|.
+     target side:  d/dr_i of phi_i, with d/dx T_n(r_A - x) = -(n_k + 1) T_{n+e_k}
+     source side:  a direct pair (i, j) gives q_i q_j d/dr_j 1/|r_j - r_i| and
+                   q_i/|r_j - r_i| to dE/dq_j; an accepted cluster A gives the
+                   adjoint lambda_A^n += q_i T_n(r_A - r_i), returned to every
+                   member k of A as sum_n lambda_A^n (r_k - r_A)^n (dE/dq_k) and
+                   q_k sum_n lambda_A^n d/dr_k (r_k - r_A)^n (dE/dr_k).
+   dEdr is n x 3, dEdq is n. */
+typedef struct {
+  double* lam;   /* n_nodes x K cluster adjoints */
+  double* src;   /* n x 3 source-side gradients (direct pairs) */
+  double* dq;    /* n source-side charge derivatives (direct pairs) */
+  double* T1;    /* Taylor coefficients up to order p + 1 */
+  int64_t target;
+  double x[3];
+  double phi;    /* phi_i */
+  double tg[3];  /* grad phi_i (target side) */
+} or_adj;
+
+static void or_adj_visit(or_sys* s, int a, or_adj* v) {
+  or_node* A = &s->nodes[a];
+  int64_t i = v->target;
+  int self = s->node_of[i * s->L + A->depth] == a;
+  int64_t Np = A->n - self;
+  if (Np == 0) return;
+  double dx = A->c[0] - v->x[0], dy = A->c[1] - v->x[1], dz = A->c[2] - v->x[2];
+  double d2 = (dx * dx + dy * dy) + dz * dz;
+  double rho2 = 3.0 * A->h * A->h;
+  int p = s->P.p, K = s->K;
+  if (Np >= s->P.N0 && rho2 <= s->theta2 * d2) {
+    /* an accepted cluster never contains its target (theta < 1), so M' = M */
+    double R[3] = {dx, dy, dz};
+    or_taylor(p + 1, R, v->T1);
+    for (int k = 0; k <= p; ++k)
+      for (int n1 = k; n1 >= 0; --n1)
+        for (int n2 = k - n1; n2 >= 0; --n2) {
+          int n3 = k - n1 - n2;
+          int t = or_term_index(n1, n2, n3);
+          double Tn = v->T1[t], Mn = A->M[t];
+          v->phi += Tn * Mn;
+          v->tg[0] -= (n1 + 1) * v->T1[or_term_index(n1 + 1, n2, n3)] * Mn;
+          v->tg[1] -= (n2 + 1) * v->T1[or_term_index(n1, n2 + 1, n3)] * Mn;
+          v->tg[2] -= (n3 + 1) * v->T1[or_term_index(n1, n2, n3 + 1)] * Mn;
+          v->lam[(int64_t)a * K + t] += s->q[i] * Tn;
+        }
+    return;
+  }
+  if (A->child >= 0 && Np > s->P.N0) {
+    for (int o = 0; o < 8; ++o) or_adj_visit(s, A->child + o, v);
+    return;
+  }
+  for (int64_t k = 0; k < A->n; ++k) {
+    int64_t j = A->idx[k];
+    if (j == i) continue;
+    double ex = s->x[3 * j] - v->x[0], ey = s->x[3 * j + 1] - v->x[1], ez = s->x[3 * j + 2] - v->x[2];
+    double r2 = (ex * ex + ey * ey) + ez * ez;
+    double r = sqrt(r2), r3 = r2 * r;
+    v->phi += s->q[j] / r;
+    /* target: d/dx q_j/|r_j - x| = q_j (r_j - x)/r^3 */
+    v->tg[0] += s->q[j] * ex / r3;
+    v->tg[1] += s->q[j] * ey / r3;
+    v->tg[2] += s->q[j] * ez / r3;
+    /* source: q_i q_j d/dr_j 1/|r_j - r_i| = -q_i q_j (r_j - r_i)/r^3 */
+    v->src[3 * j + 0] -= s->q[i] * s->q[j] * ex / r3;
+    v->src[3 * j + 1] -= s->q[i] * s->q[j] * ey / r3;
+    v->src[3 * j + 2] -= s->q[i] * s->q[j] * ez / r3;
+    v->dq[j] += s->q[i] / r;
+  }
+}
+
+int or_forces(or_sys* s, double* dEdr, double* dEdq) {
+  int K = s->K, p = s->P.p;
+  if (p + 1 > OR_PMAX) return OR_EINVAL; /* orders up to p + 1 enter the target gradient */
+  or_adj v;
+  v.lam = (double*)calloc((size_t)s->n_nodes * K, sizeof(double));
+  v.src = (double*)calloc((size_t)s->n_tot * 3, sizeof(double));
+  v.dq = (double*)calloc((size_t)s->n_tot, sizeof(double));
+  v.T1 = (double*)malloc(sizeof(double) * or_nterms(OR_PMAX));
+  double* phi = (double*)calloc((size_t)s->n_tot, sizeof(double));
+  double* tgt = (double*)calloc((size_t)s->n_tot * 3, sizeof(double));
+  for (int64_t i = 0; i < s->n_tot; ++i) {
+    v.target = i;
+    for (int c = 0; c < 3; ++c) {
+      v.x[c] = s->x[3 * i + c];
+      v.tg[c] = 0.0;
+    }
+    v.phi = 0.0;
+    or_adj_visit(s, 0, &v);
+    phi[i] = v.phi;
+    for (int c = 0; c < 3; ++c) tgt[3 * i + c] = s->q[i] * v.tg[c];
+  }
+  /* cluster adjoints back to their members: every cluster containing charge k */
+  for (int64_t k = 0; k < s->n_tot; ++k) {
+    double gq = 0.0, gr[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < s->L; ++d) {
+      int a = s->node_of[k * s->L + d];
+      if (a < 0) break;
+      or_node* A = &s->nodes[a];
+      double r[3] = {s->x[3 * k] - A->c[0], s->x[3 * k + 1] - A->c[1], s->x[3 * k + 2] - A->c[2]};
+      double px[OR_PMAX + 1], py[OR_PMAX + 1], pz[OR_PMAX + 1];
+      px[0] = py[0] = pz[0] = 1.0;
+      for (int e = 1; e <= p; ++e) {
+        px[e] = px[e - 1] * r[0];
+        py[e] = py[e - 1] * r[1];
+        pz[e] = pz[e - 1] * r[2];
+      }
+      for (int kk = 0; kk <= p; ++kk)
+        for (int n1 = kk; n1 >= 0; --n1)
+          for (int n2 = kk - n1; n2 >= 0; --n2) {
+            int n3 = kk - n1 - n2;
+            double l = v.lam[(int64_t)a * K + or_term_index(n1, n2, n3)];
+            gq += l * ((px[n1] * py[n2]) * pz[n3]);
+            if (n1) gr[0] += l * n1 * ((px[n1 - 1] * py[n2]) * pz[n3]);
+            if (n2) gr[1] += l * n2 * ((px[n1] * py[n2 - 1]) * pz[n3]);
+            if (n3) gr[2] += l * n3 * ((px[n1] * py[n2]) * pz[n3 - 1]);
+          }
+    }
+    double h = 0.5 * s->P.lB;
+    if (dEdq) dEdq[k] = h * (phi[k] + v.dq[k] + gq);
+    if (dEdr)
+      for (int c = 0; c < 3; ++c) dEdr[3 * k + c] = h * (tgt[3 * k + c] + v.src[3 * k + c] + s->q[k] * gr[c]);
+  }
+  free(v.lam);
+  free(v.src);
+  free(v.dq);
+  free(v.T1);
+  free(phi);
+  free(tgt);
+  return OR_OK;
+}

@@ -132,6 +132,11 @@ double or_energy_tree(or_sys* s);
 /* V-bar_i = l_B q_i phi_tree(r_i) and V_i = l_B q_i phi_direct(r_i) for every charge (Eq. 4.1). */
 int or_potentials(or_sys* s, double* v_tree, double* v_direct);
 
+/* Exact gradient of the total treecode energy with every MAC decision held
+   fixed: dEdr (n x 3) = dE/dr_k, dEdq (n) = dE/dq_k for every charge (ions,
+   fixed charges and images treated as independent).  Needs p <= OR_PMAX - 1. */
+int or_forces(or_sys* s, double* dEdr, double* dEdq);
+
 /* Tree export: one row per node (depth, key, is_leaf, count); leaf members are
    written consecutively into members (sorted ascending) in node order.  Returns
    the number of nodes, or -1 if a buffer is too small. */

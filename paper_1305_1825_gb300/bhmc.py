@@ -88,6 +88,7 @@ def lib():
         L.bhmc_energy.argtypes = [C.c_void_p, _dp]
         L.bhmc_energy_direct.argtypes = [C.c_void_p, _dp]
         L.bhmc_potentials.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+        L.bhmc_forces.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
         L.bhmc_export_tree.argtypes = [C.c_void_p, _i64p, C.c_int64, _i64p, C.c_int64, _dp, _i64p]
         L.bhmc_batch_create.argtypes = [C.c_int32, C.POINTER(Params), _i64p, _i64p,
                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
@@ -215,6 +216,20 @@ def bhmc_potentials(h):
     phi = np.zeros(bhmc_n_charges(h))
     _check(lib().bhmc_potentials(h, C.c_void_p(phi.ctypes.data), HOST_PTRS), "bhmc_potentials")
     return phi
+
+
+def bhmc_forces(h, dEdr=None, dEdq=None):
+    """(dE/dr (n x 3), dE/dq (n)); torch CUDA tensors given as outputs are filled in place."""
+    if dEdr is None:
+        n = bhmc_n_charges(h)
+        g = np.zeros((n, 3))
+        dq = np.zeros(n)
+        _check(lib().bhmc_forces(h, C.c_void_p(g.ctypes.data), C.c_void_p(dq.ctypes.data), HOST_PTRS),
+               "bhmc_forces")
+        return g, dq
+    _check(lib().bhmc_forces(h, C.c_void_p(dEdr.data_ptr()), C.c_void_p(dEdq.data_ptr()), DEVICE_PTRS),
+           "bhmc_forces")
+    return dEdr, dEdq
 
 
 def bhmc_get_energy(h):
@@ -349,6 +364,9 @@ class Context:
 
     def potentials(self):
         return bhmc_potentials(self.h)
+
+    def forces(self, dEdr=None, dEdq=None):
+        return bhmc_forces(self.h, dEdr, dEdq)
 
     def get_energy(self):
         return bhmc_get_energy(self.h)

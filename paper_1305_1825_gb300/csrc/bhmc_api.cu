@@ -590,6 +590,53 @@ bhmc_status bhmc_potentials(bhmc_ctx* ctx, double* phi, int32_t flags) {
   return energy_impl(ctx, nullptr, phi, flags);
 }
 
+bhmc_status bhmc_forces(bhmc_ctx* ctx, double* dEdr, double* dEdq, int32_t flags) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!dEdr || !dEdq) return BHMC_EINVAL;
+  const SysDev& S = ctx->S;
+  const size_t n = (size_t)S.n_tot;
+  const size_t nl = (size_t)S.node_cap * S.K;
+  // scratch: phi, target gradients, cluster adjoints, direct source terms, outputs
+  const size_t doubles = n + 3 * n + nl + n + 3 * n + (flags & BHMC_DEVICE_PTRS ? 0 : 4 * n);
+  double* buf = nullptr;
+  int* derr = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * doubles) != cudaSuccess) return BHMC_ENOMEM;
+  if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cudaFree(buf);
+    return BHMC_ENOMEM;
+  }
+  double* phi = buf;
+  double* tg = phi + n;
+  double* lam = tg + 3 * n;
+  double* psi = lam + nl;
+  double* src = psi + n;
+  double* odr = (flags & BHMC_DEVICE_PTRS) ? dEdr : src + 3 * n;
+  double* odq = (flags & BHMC_DEVICE_PTRS) ? dEdq : odr + 3 * n;
+  const int grid = (int)std::min<size_t>((n + 127) / 128, 152 * 16);
+  cudaError_t e = cudaMemsetAsync(lam, 0, sizeof(double) * (nl + 4 * n), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) {
+    switch (ctx->P.p) {
+      case 2: e = launch_forces<2>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
+      case 4: e = launch_forces<4>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
+      default: e = launch_forces<6>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
+    }
+  }
+  if (e == cudaSuccess) e = launch_forces_push(S, phi, tg, lam, psi, src, odr, odq, ctx->stream);
+  int herr = 0;
+  if (e == cudaSuccess && !(flags & BHMC_DEVICE_PTRS)) {
+    e = cudaMemcpyAsync(dEdr, odr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dEdq, odq, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(buf);
+  cudaFree(derr);
+  if (e != cudaSuccess) return BHMC_ECUDA;
+  return herr ? (bhmc_status)herr : BHMC_OK;
+}
+
 bhmc_status bhmc_energy_direct(bhmc_ctx* ctx, double* E) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;

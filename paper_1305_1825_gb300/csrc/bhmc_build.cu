@@ -2,6 +2,7 @@
 // adjustment kernel behind bhmc_commit_move (Sec. 3.3), and direct sums.
 #include "bhmc_build.cuh"
 #include "bhmc_move.cuh"
+#include "bhmc_forces.cuh"
 
 namespace bhmc {
 
@@ -362,6 +363,13 @@ cudaError_t launch_direct_energy(const SysDev& S, double* partial, int nblk, cud
   k_direct_energy<<<nblk, 256, 0, st>>>(S.px, S.py, S.pz, S.pq, S.n_tot, partial);
   return cudaGetLastError();
 }
+cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double* tgrad, const double* lam,
+                               const double* psi, const double* src, double* dEdr, double* dEdq,
+                               cudaStream_t st) {
+  k_forces_push<<<grid_for(S.n_tot, 128), 128, 0, st>>>(S, phi, tgrad, lam, psi, src, dEdr, dEdq);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_interleave(const SysDev& S, double* q, double* xyz, cudaStream_t st) {
   k_interleave<<<grid_for(S.n_tot, 256), 256, 0, st>>>(S, q, xyz);
   return cudaGetLastError();

@@ -5,6 +5,7 @@
 #include "bhmc_launch.cuh"
 #include "bhmc_move.cuh"
 #include "bhmc_energy.cuh"
+#include "bhmc_forces.cuh"
 
 namespace bhmc {
 
@@ -69,6 +70,18 @@ cudaError_t launch_energy<BHMC_P>(const SysDev& S, int warps, int grid, double* 
     k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
   else
     k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_forces<BHMC_P>(const SysDev& S, int grid, double* phi, double* tgrad, double* lam,
+                                  double* psi, double* src, int* err, cudaStream_t st) {
+  if (S.prec == BHMC_PREC_F64)
+    k_forces_traverse<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 128, 0, st>>>(S, S.order, phi, tgrad, lam, psi, src, err);
+  else if (S.layout == BHMC_LAYOUT_AOS)
+    k_forces_traverse<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 128, 0, st>>>(S, S.order, phi, tgrad, lam, psi, src, err);
+  else
+    k_forces_traverse<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 128, 0, st>>>(S, S.order, phi, tgrad, lam, psi, src, err);
   return cudaGetLastError();
 }
 

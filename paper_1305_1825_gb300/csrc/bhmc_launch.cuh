@@ -26,6 +26,13 @@ template <int P>
 cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial, double* phi, int* err,
                           cudaStream_t st);
 
+template <int P>
+cudaError_t launch_forces(const SysDev& S, int grid, double* phi, double* tgrad, double* lam, double* psi,
+                          double* src, int* err, cudaStream_t st);
+cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double* tgrad, const double* lam,
+                               const double* psi, const double* src, double* dEdr, double* dEdq,
+                               cudaStream_t st);
+
 #define BHMC_EXTERN_P(P)                                                                         \
   template <> cudaError_t launch_delta<P>(const SysDev&, int, int, const double*, DeltaOut*, \
                                               cudaStream_t);                                     \
@@ -36,7 +43,9 @@ cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial,
                                               const BatchArgs*, int*, bhmc_mc_stats*,            \
                                               cudaStream_t);                                     \
   template <> int batch_occupancy<P>(const SysDev&, int);                                    \
-  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, cudaStream_t);
+  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, cudaStream_t); \
+  template <> cudaError_t launch_forces<P>(const SysDev&, int, double*, double*, double*, double*, double*, int*, \
+                                           cudaStream_t);
 
 BHMC_EXTERN_P(2)
 BHMC_EXTERN_P(4)

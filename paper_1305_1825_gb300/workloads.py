@@ -136,3 +136,14 @@ def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8)
     xyz = np.concatenate([xyz, np.zeros((1, 3))], axis=0)
     return dict(name="edl-N%d" % n, params=params, q=q, xyz=xyz, n_mobile=n, n_fixed=1,
                 step=1.0, seed=seed)
+
+
+def colloid_scaled(n: int = 100000, seed: int = 7, theta: float = 0.5, p: int = 4) -> dict:
+    """The colloid radial law scaled to n ions: lengths R and r_max times
+    s = (n / 1e4)^(1/3), macroion charge Z times s^2 (nearest value with n - |Z|
+    even), decay length 2 kept."""
+    s = (n / 1e4) ** (1.0 / 3.0)
+    nz = int(round(60 * s * s))
+    if (n - nz) % 2:
+        nz += 1
+    return colloid(n=n, seed=seed, R=10.0 * s, Z=-float(nz), rmax=50.0 * s, theta=theta, p=p)

@@ -342,3 +342,44 @@ def test_relative_error_decreases_with_order(oracle_mod):
     for p in (0, 2, 4):
         assert errs[(0.3, p)] < errs[(0.5, p)]
     assert errs[(0.5, 2)] < 0.01 and errs[(0.3, 2)] < 0.001
+
+
+# ---------------------------------------------------------------- adjoint (forces)
+def test_forces_euler_identity_and_finite_differences(oracle_mod):
+    """E_tree is a quadratic form in the charges: sum_k q_k dE/dq_k = 2E exactly;
+    dE/dr and dE/dq agree with FP64 central differences of the rebuilt treecode
+    energy (h = 1e-6, where no MAC decision of these targets flips)."""
+    wl = W.plain(n=300, seed=3)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"])
+    g, dq = s.forces()
+    assert float(wl["q"] @ dq) == pytest.approx(2.0 * s.energy_tree(), rel=1e-12)
+
+    def et(xyz, q):
+        return oracle_mod.System(wl["params"], q, xyz, len(q)).energy_tree()
+    h = 1e-6
+    for k in (0, 5, 77, 210):
+        for c in range(3):
+            xp, xm = wl["xyz"].copy(), wl["xyz"].copy()
+            xp[k, c] += h
+            xm[k, c] -= h
+            assert g[k, c] == pytest.approx((et(xp, wl["q"]) - et(xm, wl["q"])) / (2 * h), abs=1e-6)
+        qp, qm = wl["q"].copy(), wl["q"].copy()
+        qp[k] += h
+        qm[k] -= h
+        assert dq[k] == pytest.approx((et(wl["xyz"], qp) - et(wl["xyz"], qm)) / (2 * h), abs=1e-6)
+
+
+def test_forces_theta_zero_equal_direct_sum(oracle_mod):
+    """theta = 0 (all pairs direct): dE/dr_k = -l_B q_k sum_j q_j (r_k - r_j)/r^3 and
+    dE/dq_k = l_B sum_j q_j / r_kj, written out from Eq. (1.1)."""
+    wl = W.colloid(n=120, seed=4, theta=0.0)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    g, dq = s.forces()
+    q, x = s.charges()
+    d = x[:, None, :] - x[None, :, :]
+    r = np.linalg.norm(d, axis=2)
+    np.fill_diagonal(r, np.inf)
+    want_r = -(q[:, None, None] * q[None, :, None] * d / r[:, :, None] ** 3).sum(axis=1)
+    want_q = (q[None, :] / r).sum(axis=1)
+    assert np.allclose(g, want_r, rtol=1e-10, atol=1e-12)
+    assert np.allclose(dq, want_q, rtol=1e-10, atol=1e-12)
