@@ -109,6 +109,10 @@ def lib():
         L.or_energy_tree.restype = C.c_double
         L.or_potentials.argtypes = [C.c_void_p, _dp, _dp]
         L.or_forces.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_ion_energy_grad.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, _dp]
+        L.or_phi_grad.argtypes = [C.c_void_p, _dp, C.c_int, _i64p, _dp, _dp]
+        L.or_mala_run.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64,
+                                  C.c_double, C.c_void_p, _i64p]
         L.or_export_tree.argtypes = [C.c_void_p, _i64p, C.c_int64, _i64p, C.c_int64]
         L.or_export_tree.restype = C.c_int64
         L.or_check.argtypes = [C.c_void_p]
@@ -248,6 +252,29 @@ class System:
         acc = C.c_int64(0)
         lib().or_mc_run(self._h, seed, replica, m0, n_moves, step,
                         recs.ctypes.data_as(C.c_void_p), C.byref(acc))
+        return recs
+
+    def phi_grad(self, x, excl=()):
+        x, xp = _d(x)
+        ex = np.ascontiguousarray(excl, dtype=np.int64)
+        phi = C.c_double(0)
+        g = np.zeros(3)
+        lib().or_phi_grad(self._h, xp, len(ex), ex.ctypes.data_as(_i64p), C.byref(phi),
+                          g.ctypes.data_as(_dp))
+        return phi.value, g
+
+    def ion_energy_grad(self, i, x):
+        x, xp = _d(x)
+        U = C.c_double(0)
+        g = np.zeros(3)
+        lib().or_ion_energy_grad(self._h, int(i), xp, C.byref(U), g.ctypes.data_as(_dp))
+        return U.value, g
+
+    def mala_run(self, seed, n_moves, tau=0.05, m0=0, replica=0):
+        recs = np.zeros(n_moves, dtype=RECORD_DTYPE)
+        acc = C.c_int64(0)
+        lib().or_mala_run(self._h, seed, replica, m0, n_moves, tau,
+                          recs.ctypes.data_as(C.c_void_p), C.byref(acc))
         return recs
 
     def energy_direct(self) -> float:

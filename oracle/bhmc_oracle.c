@@ -1123,3 +1123,197 @@ int or_forces(or_sys* s, double* dEdr, double* dEdq) {
   free(tgt);
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Potential and its gradient at x (same traversal and exclusions as or_phi). */
+typedef struct {
+  const double* x;
+  int n_excl;
+  const int64_t* excl;
+  double phi, g[3];
+  double* T1;
+  double* Mp;
+  double* mono;
+} or_grad_ctx;
+
+static int excl_has(const or_grad_ctx* v, int64_t j) {
+  for (int k = 0; k < v->n_excl; ++k)
+    if (v->excl[k] == j) return 1;
+  return 0;
+}
+
+static void or_grad_visit(or_sys* s, int a, or_grad_ctx* v) {
+  or_node* A = &s->nodes[a];
+  int in_a = 0;
+  for (int k = 0; k < v->n_excl; ++k)
+    if (s->node_of[v->excl[k] * s->L + A->depth] == a) in_a++;
+  int64_t Np = A->n - in_a;
+  if (Np == 0) return;
+  const double* x = v->x;
+  double dx = A->c[0] - x[0], dy = A->c[1] - x[1], dz = A->c[2] - x[2];
+  double d2 = (dx * dx + dy * dy) + dz * dz;
+  double rho2 = 3.0 * A->h * A->h;
+  int p = s->P.p, K = s->K;
+  if (Np >= s->P.N0 && rho2 <= s->theta2 * d2) {
+    for (int t = 0; t < K; ++t) v->Mp[t] = A->M[t];
+    for (int k = 0; k < v->n_excl; ++k) {
+      int64_t j = v->excl[k];
+      if (s->node_of[j * s->L + A->depth] != a) continue;
+      double d[3] = {s->x[3 * j] - A->c[0], s->x[3 * j + 1] - A->c[1], s->x[3 * j + 2] - A->c[2]};
+      or_monomials(p, s->q[j], d, v->mono);
+      for (int t = 0; t < K; ++t) v->Mp[t] -= v->mono[t];
+    }
+    double R[3] = {dx, dy, dz};
+    or_taylor(p + 1, R, v->T1);
+    for (int k = 0; k <= p; ++k)
+      for (int n1 = k; n1 >= 0; --n1)
+        for (int n2 = k - n1; n2 >= 0; --n2) {
+          int n3 = k - n1 - n2;
+          double M = v->Mp[or_term_index(n1, n2, n3)];
+          v->phi += v->T1[or_term_index(n1, n2, n3)] * M;
+          v->g[0] -= (n1 + 1) * v->T1[or_term_index(n1 + 1, n2, n3)] * M;
+          v->g[1] -= (n2 + 1) * v->T1[or_term_index(n1, n2 + 1, n3)] * M;
+          v->g[2] -= (n3 + 1) * v->T1[or_term_index(n1, n2, n3 + 1)] * M;
+        }
+    return;
+  }
+  if (A->child >= 0 && Np > s->P.N0) {
+    for (int o = 0; o < 8; ++o) or_grad_visit(s, A->child + o, v);
+    return;
+  }
+  for (int64_t k = 0; k < A->n; ++k) {
+    int64_t j = A->idx[k];
+    if (excl_has(v, j)) continue;
+    double ex = s->x[3 * j] - x[0], ey = s->x[3 * j + 1] - x[1], ez = s->x[3 * j + 2] - x[2];
+    double r2 = (ex * ex + ey * ey) + ez * ez, r = sqrt(r2), r3 = r2 * r;
+    v->phi += s->q[j] / r;
+    v->g[0] += s->q[j] * ex / r3;
+    v->g[1] += s->q[j] * ey / r3;
+    v->g[2] += s->q[j] * ez / r3;
+  }
+}
+
+int or_phi_grad(or_sys* s, const double x[3], int n_excl, const int64_t* excl, double* phi, double g[3]) {
+  if (s->P.p + 1 > OR_PMAX) return OR_EINVAL;
+  double T1[286], Mp[286], mono[286];
+  or_grad_ctx v = {x, n_excl, excl, 0.0, {0.0, 0.0, 0.0}, T1, Mp, mono};
+  or_grad_visit(s, 0, &v);
+  *phi = v.phi;
+  g[0] = v.g[0];
+  g[1] = v.g[1];
+  g[2] = v.g[2];
+  return OR_OK;
+}
+
+/* Single-ion energy U(x) = l_B [q phi(x) + q'(x) phi(x'(x)) + q q'(x)/|x - x'(x)|]
+   on the pre-move tree with the ion and its image excluded, and its gradient.
+   The image rule x' = R^2 x/|x|^2, q' = alpha q R/|x| gives
+   grad q' = -q' x/|x|^2, d x'/d x = (R^2/|x|^2)(I - 2 x x^T/|x|^2) and a pair
+   term alpha q^2 R/(|x|^2 - R^2). */
+static int or_ion_energy(or_sys* s, int64_t i, const double x[3], double* U, double gU[3]) {
+  int64_t excl[2] = {i, img_index(s, i)};
+  int n_excl = s->P.images ? 2 : 1;
+  double q = s->q[i], phi, g[3];
+  or_phi_grad(s, x, n_excl, excl, &phi, g);
+  double u = q * phi;
+  double gu[3] = {q * g[0], q * g[1], q * g[2]};
+  if (s->P.images) {
+    double xi[3], qi;
+    if (or_image_of(s, x, q, xi, &qi) != OR_OK) return OR_EDOMAIN;
+    double phi2, g2[3];
+    or_phi_grad(s, xi, n_excl, excl, &phi2, g2);
+    double R = s->P.image_R, al = s->P.image_alpha;
+    double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+    u += qi * phi2;
+    double dx[3] = {x[0] - xi[0], x[1] - xi[1], x[2] - xi[2]};
+    u += q * qi / sqrt((dx[0] * dx[0] + dx[1] * dx[1]) + dx[2] * dx[2]);
+    double f = R * R / r2;
+    double xg = (x[0] * g2[0] + x[1] * g2[1]) + x[2] * g2[2];
+    double pden = r2 - R * R;
+    for (int c = 0; c < 3; ++c) {
+      double jt = f * (g2[c] - 2.0 * x[c] * xg / r2); /* (dx'/dx)^T grad phi(x') */
+      gu[c] += qi * jt - phi2 * qi * x[c] / r2;     /* q' J^T grad phi(x') + phi(x') grad q' */
+      gu[c] += -al * q * q * R * 2.0 * x[c] / (pden * pden);
+    }
+  }
+  *U = s->P.lB * u;
+  for (int c = 0; c < 3; ++c) gU[c] = s->P.lB * gu[c];
+  return OR_OK;
+}
+
+/* Metropolis-adjusted Langevin single-ion moves: b = a - tau beta grad U(a) +
+   sqrt(2 tau) xi (xi from Box-Muller on Philox block (m, replica, 2)), accepted
+   iff ln alpha <= -beta (U(b) - U(a)) - |a - b + tau beta grad U(b)|^2/(4 tau)
+   + |b - a + tau beta grad U(a)|^2/(4 tau). */
+int or_mala_run(or_sys* s, uint64_t seed, uint32_t replica, uint64_t m0, int64_t n_moves, double tau,
+                or_record* recs, int64_t* n_accepted) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int64_t acc = 0;
+  if (n_moves > 0 && s->n_mob < 1) return OR_EINVAL;
+  if (s->P.p + 1 > OR_PMAX) return OR_EINVAL;
+  const double two_pi = 6.283185307179586;
+  for (int64_t t = 0; t < n_moves; ++t) {
+    uint64_t mm = m0 + (uint64_t)t;
+    uint32_t ctr[4] = {(uint32_t)mm, (uint32_t)(mm >> 32), replica, 0u};
+    uint32_t u[4], v[4], w[4];
+    or_philox4x32_10(ctr, key, u);
+    ctr[3] = 1u;
+    or_philox4x32_10(ctr, key, v);
+    ctr[3] = 2u;
+    or_philox4x32_10(ctr, key, w);
+    int64_t i = (int64_t)(((uint64_t)u[0] * (uint64_t)s->n_mob) >> 32);
+    double un[4];
+    for (int k = 0; k < 4; ++k) un[k] = ((double)w[k] + 0.5) * 0x1p-32;
+    double rad0 = sqrt(-2.0 * log(un[0])), rad1 = sqrt(-2.0 * log(un[2]));
+    double xi[3] = {rad0 * cos(two_pi * un[1]), rad0 * sin(two_pi * un[1]), rad1 * cos(two_pi * un[3])};
+    double a[3] = {s->x[3 * i], s->x[3 * i + 1], s->x[3 * i + 2]};
+    double Ua, ga[3], b[3];
+    or_record r;
+    memset(&r, 0, sizeof r);
+    r.i = i;
+    double alpha = ((double)v[0] + 0.5) * 0x1p-32;
+    r.log_alpha = log(alpha);
+    or_ion_energy(s, i, a, &Ua, ga);
+    double sd = sqrt(2.0 * tau), tb = tau * s->P.beta;
+    for (int c = 0; c < 3; ++c) b[c] = (a[c] - tb * ga[c]) + sd * xi[c];
+    memcpy(r.r_new, b, sizeof b);
+    or_move mv;
+    int st = prepare_move(s, i, b, &mv);
+    if (st == OR_EDOMAIN) {
+      r.outcome = OR_REJECT_DOMAIN;
+    } else if (st == OR_EOVERLAP) {
+      r.outcome = OR_REJECT_OVERLAP;
+    } else {
+      double Ub, gb[3];
+      or_ion_energy(s, i, b, &Ub, gb);
+      double dE = Ub - Ua;
+      double fwd = 0.0, rev = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double f = b[c] - a[c] + tb * ga[c];
+        double g = a[c] - b[c] + tb * gb[c];
+        fwd += f * f;
+        rev += g * g;
+      }
+      double lacc = -s->P.beta * dE - rev / (4.0 * tau) + fwd / (4.0 * tau);
+      r.dE = dE;
+      r.flagged = fabs(lacc - r.log_alpha) < 1e-6;
+      if (!(r.log_alpha <= lacc)) {
+        r.outcome = OR_REJECT_ENERGY;
+      } else if (or_capacity_violation(s, i, b)) {
+        r.outcome = OR_REJECT_CAPACITY;
+      } else {
+        or_commit_move(s, i, b);
+        r.outcome = OR_ACCEPT;
+        acc++;
+      }
+    }
+    if (recs) recs[t] = r;
+  }
+  if (n_accepted) *n_accepted = acc;
+  return OR_OK;
+}
+
+int or_ion_energy_grad(or_sys* s, int64_t i, const double x[3], double* U, double gU[3]) {
+  if (i < 0 || i >= s->n_mob) return OR_EINVAL;
+  return or_ion_energy(s, i, x, U, gU);
+}

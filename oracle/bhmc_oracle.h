@@ -137,6 +137,16 @@ int or_potentials(or_sys* s, double* v_tree, double* v_direct);
    fixed charges and images treated as independent).  Needs p <= OR_PMAX - 1. */
 int or_forces(or_sys* s, double* dEdr, double* dEdq);
 
+/* Potential and its gradient at x from all charges except the listed ones. */
+int or_phi_grad(or_sys* s, const double x[3], int n_excl, const int64_t* excl, double* phi, double g[3]);
+/* Single-ion energy U(x) (ion i moved to x, image following; pre-move tree with
+   both excluded) and its gradient, as used by the Langevin proposals. */
+int or_ion_energy_grad(or_sys* s, int64_t i, const double x[3], double* U, double gU[3]);
+/* Metropolis-adjusted Langevin single-ion moves (step tau); Philox blocks
+   (m, replica, 0) ion index, (m, replica, 1) alpha, (m, replica, 2) normals. */
+int or_mala_run(or_sys* s, uint64_t seed, uint32_t replica, uint64_t m0, int64_t n_moves, double tau,
+                or_record* recs, int64_t* n_accepted);
+
 /* Tree export: one row per node (depth, key, is_leaf, count); leaf members are
    written consecutively into members (sorted ascending) in node order.  Returns
    the number of nodes, or -1 if a buffer is too small. */

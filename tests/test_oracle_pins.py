@@ -383,3 +383,46 @@ def test_forces_theta_zero_equal_direct_sum(oracle_mod):
     want_q = (q[None, :] / r).sum(axis=1)
     assert np.allclose(g, want_r, rtol=1e-10, atol=1e-12)
     assert np.allclose(dq, want_q, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Langevin proposals
+def test_ion_energy_gradient_matches_delta_energy(oracle_mod):
+    """grad U (ion and its image, with the image chain rule) against central
+    differences of the oracle's own dE(i, x) = U(x) - U(a)."""
+    wl = W.colloid(n=400, seed=3)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    q, x = s.charges()
+    h = 1e-6
+    for i in (3, 50, 311):
+        pt = x[i] * 1.02
+        U, g = s.ion_energy_grad(i, pt)
+        assert U - s.ion_energy_grad(i, x[i])[0] == pytest.approx(s.delta_energy(i, pt).dE, abs=1e-12)
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = h
+            fd = (s.delta_energy(i, pt + e).dE - s.delta_energy(i, pt - e).dE) / (2 * h)
+            assert g[c] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_mala_samples_boltzmann_one_ion(oracle_mod):
+    """The Langevin chain samples the same radial density r^2 exp(-beta E(r)) as
+    the plain Metropolis chain (one ion and its image around a fixed charge)."""
+    lB, beta, Z, R, alpha = 1.0, 1.0, -4.0, 0.8, -0.3
+    params = W.base_params(lB=lB, beta=beta, shell=(1.0, 4.0), image=(R, alpha))
+    s = oracle_mod.System(params, np.array([1.0, Z]), np.array([[2.0, 0.3, -0.4], [0, 0, 0]]),
+                          n_mobile=1, n_fixed=1)
+    recs = s.mala_run(seed=78, n_moves=300000, tau=0.2)
+    r = np.empty(len(recs))
+    cur = np.linalg.norm([2.0, 0.3, -0.4])
+    for t, rec in enumerate(recs):
+        if rec["outcome"] == 0:
+            cur = np.linalg.norm(rec["r_new"])
+        r[t] = cur
+    grid = np.linspace(1.0, 4.0, 200001)
+    E = lB * (Z / grid + alpha * R / (grid ** 2 - R ** 2))
+    w = grid ** 2 * np.exp(-beta * E)
+    for f in (lambda v: v, lambda v: 1 / v, lambda v: v * v):
+        want = np.trapezoid(f(grid) * w, grid) / np.trapezoid(w, grid)
+        batches = f(r).reshape(100, -1).mean(axis=1)
+        z = (batches.mean() - want) / (batches.std(ddof=1) / 10)
+        assert abs(z) < 5, (want, batches.mean(), z)
