@@ -146,6 +146,18 @@ bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]);
 bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed,
                          uint64_t move0, bhmc_mc_stats* stats, bhmc_move_record* records);
 
+/* n_moves Metropolis-adjusted Langevin single-ion trials, one launch each: the
+   ion's energy U(x) (the potential of the tree without the ion and its image,
+   at the ion and at its image, plus the pair term) and its gradient at the
+   current position a come from one traversal; the trial position is
+   b = a - tau beta grad U(a) + sqrt(2 tau) xi with xi normal (Box-Muller on
+   Philox counter (m, 0, 2)); a second traversal gives U(b) and grad U(b); the
+   trial is accepted iff ln alpha <= -beta (U(b) - U(a)) - |a - b + tau beta
+   grad U(b)|^2 / (4 tau) + |b - a + tau beta grad U(a)|^2 / (4 tau).  Not in the
+   paper (its proposals are uniform displacements, Sec. 2). */
+bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t seed, uint64_t move0,
+                           bhmc_mc_stats* stats, bhmc_move_record* records);
+
 /* Running energy (sum of accepted dE since creation, or rebased by set). */
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E);
 bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);

@@ -83,6 +83,8 @@ def lib():
         L.bhmc_commit_move.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                    C.POINTER(McStats), C.c_void_p]
+        L.bhmc_step_mala.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
+                                     C.POINTER(McStats), C.c_void_p]
         L.bhmc_get_energy.argtypes = [C.c_void_p, _dp]
         L.bhmc_set_energy.argtypes = [C.c_void_p, C.c_double]
         L.bhmc_energy.argtypes = [C.c_void_p, _dp]
@@ -197,6 +199,14 @@ def bhmc_step_mc(h, n_moves, step, seed, move0=0, records=False):
     rec = np.zeros(n_moves, dtype=RECORD_DTYPE) if records else None
     rp = C.c_void_p(rec.ctypes.data) if records and n_moves else C.c_void_p(0)
     _check(lib().bhmc_step_mc(h, n_moves, step, seed, move0, C.byref(st), rp), "bhmc_step_mc")
+    return st, rec
+
+
+def bhmc_step_mala(h, n_moves, tau, seed, move0=0, records=False):
+    st = McStats()
+    rec = np.zeros(n_moves, dtype=RECORD_DTYPE) if records else None
+    rp = C.c_void_p(rec.ctypes.data) if records and n_moves else C.c_void_p(0)
+    _check(lib().bhmc_step_mala(h, n_moves, tau, seed, move0, C.byref(st), rp), "bhmc_step_mala")
     return st, rec
 
 
@@ -355,6 +365,9 @@ class Context:
 
     def step_mc(self, n_moves, step, seed, move0=0, records=False):
         return bhmc_step_mc(self.h, n_moves, step, seed, move0, records)
+
+    def step_mala(self, n_moves, tau, seed, move0=0, records=False):
+        return bhmc_step_mala(self.h, n_moves, tau, seed, move0, records)
 
     def energy(self):
         return bhmc_energy(self.h)

@@ -509,6 +509,42 @@ bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t 
   return BHMC_OK;
 }
 
+bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t seed, uint64_t move0,
+                           bhmc_mc_stats* stats, bhmc_move_record* records) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  if (!stats || !(tau > 0.0)) return BHMC_EINVAL;
+  if (n_moves > 0 && ctx->S.n_mob < 1) return BHMC_EINVAL;
+  IoBlock* dio = static_cast<IoBlock*>(ctx->io);
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  MoveRec* drec = nullptr;
+  if (records && n_moves) {
+    if (cudaMalloc(&drec, sizeof(MoveRec) * n_moves) != cudaSuccess) return BHMC_ENOMEM;
+  }
+  CK(cudaMemsetAsync(&dio->stats, 0, sizeof(bhmc_mc_stats), ctx->stream));
+  for (uint64_t t = 0; t < n_moves; ++t) {
+    cudaError_t e;
+    switch (ctx->P.p) {
+      case 2: e = launch_step_mala<2>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
+      case 4: e = launch_step_mala<4>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
+      default: e = launch_step_mala<6>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
+    }
+    if (e != cudaSuccess) {
+      cudaFree(drec);
+      ctx->sticky = BHMC_ECUDA;
+      return BHMC_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(&hio->stats, &dio->stats, sizeof(bhmc_mc_stats), cudaMemcpyDeviceToHost, ctx->stream));
+  if (drec)
+    CK(cudaMemcpyAsync(records, drec, sizeof(MoveRec) * n_moves, cudaMemcpyDeviceToHost, ctx->stream));
+  rc = sync_err(ctx);
+  cudaFree(drec);
+  if (rc != BHMC_OK) return rc;
+  *stats = hio->stats;
+  return BHMC_OK;
+}
+
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E) {
   if (!ctx || !E) return BHMC_EINVAL;
   CK(cudaMemcpyAsync(E, ctx->S.energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

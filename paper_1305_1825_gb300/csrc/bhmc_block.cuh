@@ -50,11 +50,14 @@ struct BlockStore {
   int wcnt[BHMC_MAX_WARPS][3];
   double wsum[BHMC_MAX_WARPS];
   int wred[BHMC_MAX_WARPS][5];
+  double wg[BHMC_MAX_WARPS][8];
 };
 
 // `path` (may be null) receives per point and level the cluster containing the
 // point; `leafcnt[s]` the count of point s's leaf when the traversal reaches it.
-template <int P, typename Real, int LAYOUT>
+// GRAD: instead of the weighted sum, accumulate the potential and its
+// gradient per role (ion point, image point).
+template <int P, typename Real, int LAYOUT, bool GRAD = false>
 __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B, unsigned pmask,
                                int (*path)[BHMC_MAX_D + 1], int* leafcnt, TravOut& out) {
   const unsigned FULL = 0xffffffffu;
@@ -63,6 +66,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   const int g = tid >> 3;
   const unsigned lt = lanemask_lt();
   Acc<Real> acc;
+  GradAcc<Real> ga;
   int visited = 0, accepted = 0, pairs = 0, fp64 = 0, err = 0;
   int cp = 1;
   while (cp < S.C) cp <<= 1;
@@ -231,17 +235,31 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     for (int k = tid; k < tm; k += nth) {
       const unsigned it = B.mi[k];
       const int s = (int)(it & 3u);
-      const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
-      acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
+      if (GRAD) {
+        Real v, g0, g1, g2;
+        eval_item_grad<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u, v, g0, g1, g2);
+        ga.add(s, v, g0, g1, g2);
+      } else {
+        const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
+        acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
+      }
     }
-    if (have0) direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
+    if (have0) {
+      if (GRAD)
+        direct_slot_grad<Real>(S, T, sa0, sb0, di0.y & 15u, ga, pairs);
+      else
+        direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
+    }
     for (int base = per; base < td; base += per) {
       const int item = base + (tid >> lg);
       if (item < td) {
         const uint2 di = B.di[item];
         if (kk < (int)(di.y >> 4)) {
           const int slot = (int)di.x * SC + kk;
-          direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
+          if (GRAD)
+            direct_slot_grad<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, ga, pairs);
+          else
+            direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
         }
       }
     }
@@ -258,11 +276,28 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   double v = acc.value();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  double gg[8];
+  if (GRAD) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      gg[4 * r] = ga.phi[r].value();
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gg[4 * r + 1 + c] = (double)ga.g[r][c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) gg[u] += __shfl_xor_sync(FULL, gg[u], o);
+  }
   const int r0 = __reduce_add_sync(FULL, visited), r1 = __reduce_add_sync(FULL, accepted);
   const int r2 = __reduce_add_sync(FULL, pairs), r3 = __reduce_add_sync(FULL, fp64);
   const int r4 = __reduce_max_sync(FULL, err);
   if (lane == 0) {
     B.wsum[warp] = v;
+    if (GRAD) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) B.wg[warp][u] = gg[u];
+    }
     B.wred[warp][0] = r0;
     B.wred[warp][1] = r1;
     B.wred[warp][2] = r2;
@@ -272,9 +307,18 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   __syncthreads();
   if (tid == 0) {
     out.sum = 0.0;
+    for (int r = 0; r < 2; ++r) {
+      out.phi[r] = 0.0;
+      out.grad[r][0] = out.grad[r][1] = out.grad[r][2] = 0.0;
+    }
     out.visited = out.accepted = out.pairs = out.fp64 = out.err = 0;
     for (int w = 0; w < NW; ++w) {
       out.sum += B.wsum[w];
+      if (GRAD)
+        for (int r = 0; r < 2; ++r) {
+          out.phi[r] += B.wg[w][4 * r];
+          for (int c = 0; c < 3; ++c) out.grad[r][c] += B.wg[w][4 * r + 1 + c];
+        }
       out.visited += B.wred[w][0];
       out.accepted += B.wred[w][1];
       out.pairs += B.wred[w][2];

@@ -37,6 +37,20 @@ cudaError_t launch_step<BHMC_P>(const SysDev& S, int warps, unsigned long long m
 }
 
 template <>
+cudaError_t launch_step_mala<BHMC_P>(const SysDev& S, int warps, unsigned long long m, unsigned replica,
+                                     unsigned long long seed, double tau, MoveRec* rec, bhmc_mc_stats* stats,
+                                     cudaStream_t st) {
+  const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+  if (S.prec == BHMC_PREC_F64)
+    k_step_mala<BHMC_P, double, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, m, replica, key, tau, rec, stats);
+  else if (S.layout == BHMC_LAYOUT_AOS)
+    k_step_mala<BHMC_P, float, BHMC_LAYOUT_AOS><<<1, 32 * warps, 0, st>>>(S, m, replica, key, tau, rec, stats);
+  else
+    k_step_mala<BHMC_P, float, BHMC_LAYOUT_SOA><<<1, 32 * warps, 0, st>>>(S, m, replica, key, tau, rec, stats);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_batch<BHMC_P>(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
                                  const BatchArgs* args, int* next, bhmc_mc_stats* stats,
                                  cudaStream_t st) {

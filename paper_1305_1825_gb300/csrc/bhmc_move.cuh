@@ -27,6 +27,9 @@ struct MoveSh {
   int outcome, flagged, go;
   int rej_dom, rej_shell, rej_img;
   double dE, alpha;
+  double xi[3];            // Langevin proposals: normal variates
+  double U[2], gU[2][3];   // single-ion energy and gradient at the old / new position
+  double tphi[2], tgrad[2][3];  // per-role potential and gradient of the last gradient traversal
   int split_node, split_g;
   unsigned char ex[nterms(BHMC_MAX_P)][3];  // exponents of every moment term
   float4 tA[BHMC_MAX_C + 2], tB[BHMC_MAX_C + 2];
@@ -627,6 +630,149 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
   return sh.outcome;
 }
 
+// ---------------------------------------------------------------------------
+// Metropolis-adjusted Langevin single-ion moves.  The single-ion energy is
+//   U(x) = l_B [q phi(x) + q'(x) phi(x'(x)) + q q'(x) / |x - x'(x)|]
+// on the pre-move tree with the ion and its image excluded (so that
+// dE = U(b) - U(a) is the trial move's energy difference), with
+// x' = R^2 x/|x|^2, q' = alpha q R/|x|:
+//   grad U = l_B [q grad phi(x) + q' J^T grad phi(x') + phi(x') grad q' + grad P],
+//   J = (R^2/|x|^2)(I - 2 x x^T/|x|^2), grad q' = -q' x/|x|^2,
+//   P = alpha q^2 R / (|x|^2 - R^2), grad P = -2 alpha q^2 R x / (|x|^2 - R^2)^2.
+
+// One gradient traversal over the points of pmask; results in sh.tphi, sh.tgrad.
+template <int P, typename Real, int LAYOUT>
+__device__ bool eval_grad(const SysDev& S, MoveStore& st, unsigned pmask) {
+  MoveSh& sh = st.sh;
+  for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x)
+    if ((pmask >> (k / (BHMC_MAX_D + 1))) & 1u) (&sh.path[0][0])[k] = -1;
+  if (threadIdx.x < 4 && ((pmask >> threadIdx.x) & 1u)) sh.leafcnt[threadIdx.x] = -1;
+  __syncthreads();
+  TravOut o;
+  block_traverse<P, Real, LAYOUT, true>(S, sh.T, st.bs, pmask, sh.path, sh.leafcnt, o);
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < 2; ++r) {
+      sh.tphi[r] = o.phi[r];
+      for (int c = 0; c < 3; ++c) sh.tgrad[r][c] = o.grad[r][c];
+    }
+    sh.cnt[0][4] = o.err;
+  }
+  __syncthreads();
+  return sh.cnt[0][4] == 0;
+}
+
+// U and grad U at x (image xi, image charge qimg) from a gradient traversal (thread 0).
+__device__ __forceinline__ void ion_energy(const SysDev& S, const MoveSh& sh, const double x[3], const double xi[3],
+                                           double qimg, double& U, double g[3]) {
+  const double q = sh.q;
+  double u = q * sh.tphi[0];
+  for (int c = 0; c < 3; ++c) g[c] = q * sh.tgrad[0][c];
+  if (S.images) {
+    const double* g2 = sh.tgrad[1];
+    const double R = S.img_R;
+    const double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+    u += qimg * sh.tphi[1];
+    const double dx = x[0] - xi[0], dy = x[1] - xi[1], dz = x[2] - xi[2];
+    u += q * qimg / sqrt((dx * dx + dy * dy) + dz * dz);
+    const double f = R * R / r2;
+    const double xg = (x[0] * g2[0] + x[1] * g2[1]) + x[2] * g2[2];
+    const double pden = r2 - R * R;
+    for (int c = 0; c < 3; ++c) {
+      g[c] += qimg * (f * (g2[c] - 2.0 * x[c] * xg / r2)) - sh.tphi[1] * qimg * x[c] / r2;
+      g[c] += -S.img_alpha * q * q * R * 2.0 * x[c] / (pden * pden);
+    }
+  }
+  U = S.lB * u;
+  for (int c = 0; c < 3; ++c) g[c] *= S.lB;
+}
+
+template <int P, typename Real, int LAYOUT>
+__device__ int mala_move(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica, uint2 key,
+                         double tau, MoveRec* rec) {
+  MoveSh& sh = st.sh;
+  if (threadIdx.x == 0) {
+    const uint4 u = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 0u), key);
+    const uint4 v = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 1u), key);
+    const uint4 w = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 2u), key);
+    const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
+    const double un0 = ((double)w.x + 0.5) * 0x1p-32, un1 = ((double)w.y + 0.5) * 0x1p-32;
+    const double un2 = ((double)w.z + 0.5) * 0x1p-32, un3 = ((double)w.w + 0.5) * 0x1p-32;
+    const double two_pi = 6.283185307179586;
+    const double rad0 = sqrt(-2.0 * log(un0)), rad1 = sqrt(-2.0 * log(un2));
+    sh.xi[0] = rad0 * cos(two_pi * un1);
+    sh.xi[1] = rad0 * sin(two_pi * un1);
+    sh.xi[2] = rad1 * cos(two_pi * un3);
+    sh.alpha = ((double)v.x + 0.5) * 0x1p-32;
+    sh.i = i;
+    sh.b[0] = S.px[i];
+    sh.b[1] = S.py[i];
+    sh.b[2] = S.pz[i];
+    sh.dE = 0.0;
+    sh.flagged = 0;
+  }
+  __syncthreads();
+  setup_move(S, sh);  // points at the current position (b = a) for the first traversal
+  __syncthreads();
+  if (!eval_grad<P, Real, LAYOUT>(S, st, sh.npts == 4 ? 5u : 1u)) {
+    if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
+    return -1;
+  }
+  if (threadIdx.x == 0) {
+    ion_energy(S, sh, sh.a, sh.ai, sh.qa_img, sh.U[0], sh.gU[0]);
+    const double tb = tau * S.beta, sd = sqrt(2.0 * tau);
+    for (int c = 0; c < 3; ++c)
+      sh.b[c] = __dadd_rn(__dsub_rn(sh.a[c], __dmul_rn(tb, sh.gU[0][c])), __dmul_rn(sd, sh.xi[c]));
+  }
+  __syncthreads();
+  setup_move(S, sh);
+  __syncthreads();
+  if (sh.outcome < 0) {
+    if (!eval_grad<P, Real, LAYOUT>(S, st, sh.npts == 4 ? 10u : 2u)) {
+      if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
+      return -1;
+    }
+    complete_paths(S, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ion_energy(S, sh, sh.b, sh.bi, sh.qb_img, sh.U[1], sh.gU[1]);
+      sh.dE = sh.U[1] - sh.U[0];
+      const double tb = tau * S.beta;
+      double fwd = 0.0, rev = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double f = sh.b[c] - sh.a[c] + tb * sh.gU[0][c];
+        const double g = sh.a[c] - sh.b[c] + tb * sh.gU[1][c];
+        fwd += f * f;
+        rev += g * g;
+      }
+      const double lacc = -S.beta * sh.dE - rev / (4.0 * tau) + fwd / (4.0 * tau);
+      const double la = log(sh.alpha);
+      sh.flagged = fabs(lacc - la) < 1e-6 ? 1 : 0;
+      if (!(la <= lacc))
+        sh.outcome = BHMC_REJECT_ENERGY;
+      else if (capacity_violation(S, sh))
+        sh.outcome = BHMC_REJECT_CAPACITY;
+      else
+        sh.outcome = BHMC_ACCEPT;
+    }
+    __syncthreads();
+    if (sh.outcome == BHMC_ACCEPT) {
+      commit_move_block(S, st);
+      if (threadIdx.x == 0) *S.energy += sh.dE;
+    }
+  }
+  if (threadIdx.x == 0 && rec) {
+    rec->i = sh.i;
+    rec->r[0] = sh.b[0];
+    rec->r[1] = sh.b[1];
+    rec->r[2] = sh.b[2];
+    rec->dE = sh.dE;
+    rec->outcome = sh.outcome;
+    rec->flagged = sh.flagged;
+  }
+  __syncthreads();
+  return sh.outcome;
+}
+
 __device__ __forceinline__ void tally(bhmc_mc_stats* st, int outcome, int flagged) {
   st->moves += 1;
   if (outcome == BHMC_ACCEPT) st->accepted += 1;
@@ -680,6 +826,19 @@ __global__ void __launch_bounds__(256) k_step(SysDev S, unsigned long long m, un
   if (*(volatile int*)S.err) return;
   init_tables(st.sh, S.K);
   const int o = mc_move<P, Real, LAYOUT>(S, st, m, replica, key, step, recs);
+  if (threadIdx.x == 0 && o >= 0) {
+    tally(stats, o, st.sh.flagged);
+    stats->energy = *S.energy;
+  }
+}
+
+template <int P, typename Real, int LAYOUT>
+__global__ void __launch_bounds__(256) k_step_mala(SysDev S, unsigned long long m, unsigned replica, uint2 key,
+                                                   double tau, MoveRec* recs, bhmc_mc_stats* stats) {
+  __shared__ MoveStore st;
+  if (*(volatile int*)S.err) return;
+  init_tables(st.sh, S.K);
+  const int o = mala_move<P, Real, LAYOUT>(S, st, m, replica, key, tau, recs);
   if (threadIdx.x == 0 && o >= 0) {
     tally(stats, o, st.sh.flagged);
     stats->energy = *S.energy;

@@ -34,6 +34,11 @@ struct TravPts {
 
 struct TravOut {
   double sum;
+  // gradient traversals: potential and its gradient per role, role 0 the
+  // points 0 and 1 (ion), role 1 the points 2 and 3 (image); a traversal
+  // evaluates at most one point of each role
+  double phi[2];
+  double grad[2][3];
   int visited, accepted, pairs, fp64;
   int err;
 };
@@ -99,6 +104,97 @@ __device__ __forceinline__ R dot_monomials(const R (&T)[nterms(P)], R dx, R dy, 
 #pragma unroll
       for (int n2 = k - n1; n2 >= 0; --n2) v += T[tidx(n1, n2, k - n1 - n2)] * (px[n1] * py[n2] * pz[k - n1 - n2]);
   return v;
+}
+
+// Value and gradient with respect to the evaluation point of the p-th order
+// expansion of one charge at offset d from the cluster centre, from Taylor
+// coefficients up to order p + 1: d/dx T_n(r_A - x) = -(n_c + 1) T_{n + e_c}.
+template <int P, typename R>
+__device__ __forceinline__ void dot_monomials_grad(const R (&T)[nterms(P + 1)], R dx, R dy, R dz, R& v,
+                                                   R& g0, R& g1, R& g2) {
+  R px[P + 1], py[P + 1], pz[P + 1];
+  px[0] = py[0] = pz[0] = R(1);
+#pragma unroll
+  for (int k = 1; k <= P; ++k) {
+    px[k] = px[k - 1] * dx;
+    py[k] = py[k - 1] * dy;
+    pz[k] = pz[k - 1] * dz;
+  }
+  v = g0 = g1 = g2 = R(0);
+#pragma unroll
+  for (int k = 0; k <= P; ++k)
+#pragma unroll
+    for (int n1 = k; n1 >= 0; --n1)
+#pragma unroll
+      for (int n2 = k - n1; n2 >= 0; --n2) {
+        const int n3 = k - n1 - n2;
+        const R m = px[n1] * py[n2] * pz[n3];
+        v += T[tidx(n1, n2, n3)] * m;
+        g0 -= R(n1 + 1) * T[tidx(n1 + 1, n2, n3)] * m;
+        g1 -= R(n2 + 1) * T[tidx(n1, n2 + 1, n3)] * m;
+        g2 -= R(n3 + 1) * T[tidx(n1, n2, n3 + 1)] * m;
+      }
+}
+
+// Multipole term of cluster `node` at point s and its gradient with respect to
+// the evaluation point (excluded charges removed as in eval_item).
+template <int P, typename Real, int LAYOUT>
+__device__ __forceinline__ void eval_item_grad(const SysDev& S, const TravPts& T, int node, int s, unsigned emask,
+                                               Real& v, Real& g0, Real& g1, Real& g2) {
+  constexpr int K = nterms(P);
+  const float4 a = S.nA[node];
+  Real rx, ry, rz;
+  if (sizeof(Real) == 4) {
+    rx = (Real)((a.x - T.hi[s][0]) - T.lo[s][0]);
+    ry = (Real)((a.y - T.hi[s][1]) - T.lo[s][1]);
+    rz = (Real)((a.z - T.hi[s][2]) - T.lo[s][2]);
+  } else {
+    rx = (Real)__dsub_rn((double)a.x, T.x[s][0]);
+    ry = (Real)__dsub_rn((double)a.y, T.x[s][1]);
+    rz = (Real)__dsub_rn((double)a.z, T.x[s][2]);
+  }
+  Real Tc[nterms(P + 1)];
+  taylor<P + 1, Real>(rx, ry, rz, Tc);
+  v = g0 = g1 = g2 = Real(0);
+#pragma unroll
+  for (int k = 0; k <= P; ++k)
+#pragma unroll
+    for (int n1 = k; n1 >= 0; --n1)
+#pragma unroll
+      for (int n2 = k - n1; n2 >= 0; --n2) {
+        const int n3 = k - n1 - n2;
+        const int t = tidx(n1, n2, n3);
+        Real m;
+        if (sizeof(Real) == 4)
+          m = (Real)(LAYOUT == BHMC_LAYOUT_AOS ? S.M32[(size_t)node * pad4(K) + t] : S.M32[(size_t)t * S.node_cap + node]);
+        else
+          m = (Real)S.M64[(size_t)node * K + t];
+        v += Tc[t] * m;
+        g0 -= Real(n1 + 1) * Tc[tidx(n1 + 1, n2, n3)] * m;
+        g1 -= Real(n2 + 1) * Tc[tidx(n1, n2 + 1, n3)] * m;
+        g2 -= Real(n3 + 1) * Tc[tidx(n1, n2, n3 + 1)] * m;
+      }
+  while (emask) {
+    const int k = __ffs(emask) - 1;
+    emask &= emask - 1;
+    Real dx, dy, dz;
+    if (sizeof(Real) == 4) {
+      dx = (Real)((T.ehi[k][0] - a.x) + T.elo[k][0]);
+      dy = (Real)((T.ehi[k][1] - a.y) + T.elo[k][1]);
+      dz = (Real)((T.ehi[k][2] - a.z) + T.elo[k][2]);
+    } else {
+      dx = (Real)__dsub_rn(T.ex[k][0], (double)a.x);
+      dy = (Real)__dsub_rn(T.ex[k][1], (double)a.y);
+      dz = (Real)__dsub_rn(T.ex[k][2], (double)a.z);
+    }
+    Real cv, c0, c1, c2;
+    dot_monomials_grad<P, Real>(Tc, dx, dy, dz, cv, c0, c1, c2);
+    const Real qe = sizeof(Real) == 4 ? (Real)T.eqf[k] : (Real)T.eq[k];
+    v -= qe * cv;
+    g0 -= qe * c0;
+    g1 -= qe * c1;
+    g2 -= qe * c2;
+  }
 }
 
 // Multipole term of cluster `node` at point s: sum_n T_n(r_A - x) M'_n with
@@ -182,6 +278,57 @@ struct Acc<double> {
   __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ double value() const { return s; }
 };
+
+// Potential and gradient sums of the two roles of a gradient traversal.
+template <typename Real>
+struct GradAcc {
+  Acc<Real> phi[2];
+  Real g[2][3] = {{Real(0), Real(0), Real(0)}, {Real(0), Real(0), Real(0)}};
+  __device__ __forceinline__ void add(int s, Real v, Real gx, Real gy, Real gz) {
+    if (s & 2) {
+      phi[1].add(v);
+      g[1][0] += gx;
+      g[1][1] += gy;
+      g[1][2] += gz;
+    } else {
+      phi[0].add(v);
+      g[0][0] += gx;
+      g[0][1] += gy;
+      g[0][2] += gz;
+    }
+  }
+};
+
+// Direct terms of one leaf slot against the points of `m`, with gradients
+// d/dx q_j/|r_j - x| = q_j (r_j - x)/|r_j - x|^3.
+template <typename Real>
+__device__ __forceinline__ void direct_slot_grad(const SysDev& S, const TravPts& T, float4 sa, float4 sb,
+                                                 unsigned m, GradAcc<Real>& G, int& pairs) {
+  const int j = __float_as_int(sb.w);
+  for (int u = 0; u < T.n_excl; ++u)
+    if (T.excl[u] == j) return;
+  while (m) {
+    const int s = __ffs(m) - 1;
+    m &= m - 1;
+    Real dx, dy, dz, qj;
+    if (sizeof(Real) == 4) {
+      dx = (Real)((sa.x - T.hi[s][0]) + (sb.x - T.lo[s][0]));
+      dy = (Real)((sa.y - T.hi[s][1]) + (sb.y - T.lo[s][1]));
+      dz = (Real)((sa.z - T.hi[s][2]) + (sb.z - T.lo[s][2]));
+      qj = (Real)sa.w;
+    } else {
+      dx = (Real)__dsub_rn(S.px[j], T.x[s][0]);
+      dy = (Real)__dsub_rn(S.py[j], T.x[s][1]);
+      dz = (Real)__dsub_rn(S.pz[j], T.x[s][2]);
+      qj = (Real)S.pq[j];
+    }
+    const Real r2 = dx * dx + dy * dy + dz * dz;
+    const Real rinv = sizeof(Real) == 4 ? (Real)rsqrtf((float)r2) : (Real)(1.0 / sqrt((double)r2));
+    const Real v = qj * rinv, f = v * rinv * rinv;
+    G.add(s, v, f * dx, f * dy, f * dz);
+    ++pairs;
+  }
+}
 
 // Direct terms of one leaf slot against the points of `m`.
 template <typename Real>
