@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--layout", default="aos", choices=["soa", "aos"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--suite", action="store_true",
+                    help="one JSON line per workload family instead of the headline line")
+    ap.add_argument("--suite-large", action="store_true", help="include the 1e6-ion items in --suite")
     return ap.parse_args()
 
 
@@ -340,10 +343,207 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ suite
+def _ev_time(fn):
+    """Device time (ms) of fn() on torch's current stream (the library's stream)."""
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    out = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _de_errors(bh, wl, n, seed, warps, layout):
+    """FP32-traversal dE against the FP64 GPU traversal at the same theta and p
+    (the FP64 mode equals the oracle to ~1e-16 of the interaction sums), and
+    against the exact dE (theta = 0, FP64)."""
+    import copy
+    import numpy as np
+    tree = bh.Context(wl, warps=warps, layout=layout)
+    f64 = bh.Context(wl, precision=bh.PREC_F64, warps=warps)
+    ex_wl = copy.deepcopy(wl)
+    ex_wl["params"]["theta"] = 0.0
+    exact = bh.Context(ex_wl, precision=bh.PREC_F64, warps=8)
+    rng = np.random.default_rng(seed)
+    rel32, rel_tree, num, den = [], [], 0.0, 0.0
+    for _ in range(n):
+        i = int(rng.integers(0, wl["n_mobile"]))
+        b = wl["xyz"][i] + rng.uniform(-0.5, 0.5, 3)
+        rc, d32, _ = tree.delta_energy(i, b)
+        rc2, d64, _ = f64.delta_energy(i, b)
+        rc3, dex, _ = exact.delta_energy(i, b)
+        if rc or rc2 or rc3:
+            continue
+        rel32.append(abs(d32 - d64) / max(abs(d64), 1e-300))
+        rel_tree.append(abs(d64 - dex) / max(abs(dex), 1e-300))
+        num += (d64 - dex) ** 2
+        den += dex ** 2
+    for c in (tree, f64, exact):
+        c.close()
+    rel32, rel_tree = np.array(rel32), np.array(rel_tree)
+    q = lambda a, v: float(np.quantile(a, v))
+    return {"samples": int(len(rel32)),
+            "f32_vs_f64_treecode_rel": {"median": q(rel32, 0.5), "p99": q(rel32, 0.99), "max": float(rel32.max())},
+            "treecode_vs_direct_rel": {"median": q(rel_tree, 0.5), "p99": q(rel_tree, 0.99)},
+            "E_eq4_1": float(np.sqrt(num / den))}
+
+
+def _plain_moves(bh, wl, warps, layout, moves, precision=0):
+    import torch
+    ctx = bh.Context(wl, warps=warps, layout=layout, precision=precision)
+    ctx.step_mc(20, 1.0, seed=wl.get("seed", 1), move0=0)
+    ms, _ = _ev_time(lambda: ctx.step_mc(moves, 1.0, seed=wl.get("seed", 1), move0=20))
+    ctx.close()
+    torch.cuda.synchronize()
+    return moves / (ms / 1e3)
+
+
+def _batched_moves(bh, systems, seeds, warps, layout, moves):
+    b = bh.Batch(systems, warps=warps, layout=layout)
+    b.step_mc(moves // 4, 1.0, seeds)
+    ms, st = _ev_time(lambda: b.step_mc(moves, 1.0, seeds, move0=moves // 4))
+    acc = sum(s["accepted"] for s in st) / max(sum(s["moves"] for s in st), 1)
+    b.close()
+    return len(systems) * moves / (ms / 1e3), acc
+
+
+def _oracle_moves(wl, seed, moves, budget_s):
+    import oracle
+    ref = oracle.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        ref.mc_run(seed, moves, m0=done)
+        done += moves
+    return done / (time.perf_counter() - t0)
+
+
+def _direct_forces(q, x, idx, lB):
+    """dE/dr_i = -l_B q_i sum_j q_j (r_i - r_j)/|r_i - r_j|^3 (FP64 direct sum)."""
+    import numpy as np
+    out = np.zeros((len(idx), 3))
+    for k, i in enumerate(idx):
+        d = x[i] - x
+        r2 = np.einsum("ij,ij->i", d, d)
+        r2[i] = np.inf
+        out[k] = -lB * q[i] * ((q / r2 ** 1.5)[:, None] * d).sum(axis=0)
+    return out
+
+
+def _field_item(bh, name, wl, reps=3):
+    """Full treecode energy and adjoint forces: targets/s, and forces against
+    the FP64 direct sum on 64 sampled charges."""
+    import numpy as np
+    import torch
+    ctx = bh.Context(wl, warps=8, layout=bh.LAYOUT_AOS)
+    q, x = ctx.charges()
+    n = len(q)
+    _, cnt = ctx.energy_counters()
+    ms_e = min(_ev_time(ctx.energy)[0] for _ in range(reps))
+    p = wl["params"]["p"]
+    K = (p + 1) * (p + 2) * (p + 3) // 6
+    bytes_e = 32 * cnt.visited + 4 * K * cnt.accepted + 32 * cnt.pairs
+    pk, pk_src = peaks()
+    dEdr = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    dEdq = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.forces(dEdr, dEdq)
+    ms_f = min(_ev_time(lambda: ctx.forces(dEdr, dEdq))[0] for _ in range(reps))
+    g = dEdr.cpu().numpy()
+    idx = np.random.default_rng(4).choice(len(q), 64, replace=False)
+    want = _direct_forces(q, x, idx, wl["params"].get("lB", 1.0))
+    err = np.linalg.norm(g[idx] - want, axis=1) / np.linalg.norm(want, axis=1)
+    ctx.close()
+    achieved = bytes_e / (ms_e / 1e3) / 1e9
+    return {"suite": name, "charges": int(len(q)), "energy_ms": ms_e, "energy_targets_per_s": len(q) / (ms_e / 1e3),
+            "energy_roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                "frac": achieved / pk["hbm_gbs"], "peak_source": pk_src,
+                                "bytes_per_target": bytes_e / len(q),
+                                "per_target": {"visited": cnt.visited / len(q), "multipole": cnt.accepted / len(q),
+                                               "direct_pairs": cnt.pairs / len(q)}},
+            "forces_ms": ms_f, "forces_targets_per_s": len(q) / (ms_f / 1e3),
+            "forces_vs_direct_rel": {"median": float(np.median(err)), "max": float(err.max())},
+            "theta": wl["params"]["theta"], "p": wl["params"]["p"]}
+
+
+def run_suite(args):
+    """One JSON line per workload family: the plain 2000-charge system, the 1e4
+    colloid over theta x p, adjoint forces and full energy at 1e5 (and 1e6), the
+    1e6-ion colloid, and Langevin moves.  Moves per second are CUDA-event times
+    on the library's stream; dE errors are measured on the GPU against its FP64
+    mode and the theta = 0 direct sum."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1825_gb300 import bhmc as bh
+    from paper_1305_1825_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    lines = []
+
+    def emit(d):
+        lines.append(d)
+        print(json.dumps(d), flush=True)
+
+    # plain 2000-charge system: one launch per move, FP32 and FP64 traversal
+    wl = W.plain(n=2000)
+    emit({"suite": "plain-N2000", "theta": 0.5, "p": 4, "C": 8,
+          "gpu_plain_f32_moves_per_s": _plain_moves(bh, wl, 8, bh.LAYOUT_AOS, 1000),
+          "gpu_plain_f64_moves_per_s": _plain_moves(bh, wl, 8, bh.LAYOUT_AOS, 1000, precision=bh.PREC_F64),
+          "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 1, 200, 3.0),
+          "dE_error": _de_errors(bh, wl, 200, 11, 8, bh.LAYOUT_AOS)})
+
+    # colloid, 1e4 ions: theta x p; batched = 152 replicas of the same size
+    for theta in (0.3, 0.5, 0.7):
+        for p in (2, 4, 6):
+            wl = W.colloid(n=10000, seed=2, theta=theta, p=p, C=args.C)
+            systems = [W.colloid(n=10000, seed=2000 + r, theta=theta, p=p, C=args.C) for r in range(152)]
+            rate_b, acc = _batched_moves(bh, systems, [2000 + r for r in range(152)], args.warps,
+                                         bh.LAYOUT_AOS, 400)
+            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400)
+            emit({"suite": "colloid-N1e4", "theta": theta, "p": p, "C": args.C,
+                  "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b,
+                  "batched_over_plain": rate_b / rate_p, "acceptance": acc,
+                  "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 2, 100, 2.0),
+                  "dE_error": _de_errors(bh, wl, 40, 100 + p, args.warps, bh.LAYOUT_AOS)})
+            del systems
+
+    # Langevin moves on the 1e4 colloid (step 0.05)
+    wl = W.colloid(n=10000, seed=2)
+    ctx = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
+    ctx.step_mala(20, 0.05, seed=3)
+    ms, (st, _) = _ev_time(lambda: ctx.step_mala(400, 0.05, seed=3, move0=20))
+    emit({"suite": "mala-colloid-N1e4", "tau": 0.05, "gpu_moves_per_s": 400 / (ms / 1e3),
+          "acceptance": st.accepted / max(st.moves, 1)})
+    ctx.close()
+
+    # adjoint forces and full energy
+    emit(_field_item(bh, "field-uniform-N1e5", W.uniform(n=100000)))
+    emit(_field_item(bh, "field-colloid-scaled-N1e5", W.colloid_scaled(n=100000)))
+    if args.suite_large:
+        wl = W.large()
+        emit(_field_item(bh, "field-large-N1e6", wl, reps=2))
+        ctx = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
+        ctx.step_mc(20, 1.0, seed=9)
+        ms, st = _ev_time(lambda: ctx.step_mc(500, 1.0, seed=9, move0=20))
+        ctx.close()
+        b = bh.Batch([wl], warps=args.warps, layout=bh.LAYOUT_AOS)
+        b.step_mc(100, 1.0, [9])
+        ms_b, _ = _ev_time(lambda: b.step_mc(4000, 1.0, [9], move0=100))
+        b.close()
+        emit({"suite": "large-N1e6", "theta": 0.5, "p": 6, "C": 8, "charges": 2000001,
+              "gpu_plain_moves_per_s": 500 / (ms / 1e3),
+              "gpu_persistent_1_replica_moves_per_s": 4000 / (ms_b / 1e3)})
+    return lines
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.suite:
+        run_suite(args)
     else:
         run_gpu(args)
 

@@ -165,6 +165,10 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);
 /* Total treecode energy E = (1/2) l_B sum_i q_i phi_tree(r_i), every charge
    excluded from its own sum (Eq. 1.1 evaluated by the Sec. 3.2 traversal). */
 bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E);
+/* bhmc_energy plus the interaction-list counters summed over every target
+   (visited clusters, multipole evaluations, direct pairs; mac_fp64 is 0): the
+   per-target counts are those of the Sec. 3.2 traversal at r_j with j excluded. */
+bhmc_status bhmc_energy_counters(bhmc_ctx* ctx, double* E, bhmc_counters* total);
 /* Treecode potential of every charge, phi_j = sum over the tree minus j of
    q_k / |r_k - r_j| (the traversal of Sec. 3.2 at r_j), into phi[n_charges]
    (host or device memory per flags).  The same pass as bhmc_energy. */

@@ -83,6 +83,7 @@ def lib():
         L.bhmc_commit_move.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                    C.POINTER(McStats), C.c_void_p]
+        L.bhmc_energy_counters.argtypes = [C.c_void_p, _dp, C.POINTER(Counters)]
         L.bhmc_step_mala.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                      C.POINTER(McStats), C.c_void_p]
         L.bhmc_get_energy.argtypes = [C.c_void_p, _dp]
@@ -214,6 +215,13 @@ def bhmc_energy(h):
     e = C.c_double()
     _check(lib().bhmc_energy(h, C.byref(e)), "bhmc_energy")
     return e.value
+
+
+def bhmc_energy_counters(h):
+    e = C.c_double()
+    c = Counters()
+    _check(lib().bhmc_energy_counters(h, C.byref(e), C.byref(c)), "bhmc_energy_counters")
+    return e.value, c
 
 
 def bhmc_energy_direct(h):
@@ -371,6 +379,9 @@ class Context:
 
     def energy(self):
         return bhmc_energy(self.h)
+
+    def energy_counters(self):
+        return bhmc_energy_counters(self.h)
 
     def energy_direct(self):
         return bhmc_energy_direct(self.h)

@@ -562,28 +562,32 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E) {
   return BHMC_OK;
 }
 
-static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, double* phi, int* err) {
+static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, double* phi, int* err,
+                                   unsigned long long* cnt) {
   const int w = BHMC_ENERGY_WARPS;
   switch (c->P.p) {
-    case 2: return launch_energy<2>(c->S, w, grid, partial, phi, err, c->stream);
-    case 4: return launch_energy<4>(c->S, w, grid, partial, phi, err, c->stream);
-    default: return launch_energy<6>(c->S, w, grid, partial, phi, err, c->stream);
+    case 2: return launch_energy<2>(c->S, w, grid, partial, phi, err, cnt, c->stream);
+    case 4: return launch_energy<4>(c->S, w, grid, partial, phi, err, cnt, c->stream);
+    default: return launch_energy<6>(c->S, w, grid, partial, phi, err, cnt, c->stream);
   }
 }
 
-static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_t flags) {
+static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_t flags,
+                               bhmc_counters* total = nullptr) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
   const int warps = BHMC_ENERGY_WARPS;  // each warp evaluates 32 targets at a time
   int grid = (ctx->S.n_tot + 32 * warps - 1) / (32 * warps);
   grid = std::min(grid, 152 * 16);
   double* partial = nullptr;
-  int* derr = nullptr;
+  int* derr = nullptr;  // error flag, then three counters (8-byte aligned)
   if (cudaMalloc(&partial, sizeof(double) * grid * warps) != cudaSuccess) return BHMC_ENOMEM;
-  if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&derr, 32) != cudaSuccess) {
     cudaFree(partial);
     return BHMC_ENOMEM;
   }
+  unsigned long long* dcnt = total ? reinterpret_cast<unsigned long long*>(derr) + 1 : nullptr;
+  unsigned long long hcnt[3] = {0, 0, 0};
   double* dphi = nullptr;
   if (phi_out) {
     if (flags & BHMC_DEVICE_PTRS) {
@@ -596,11 +600,13 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   }
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
-  bool ok = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream) == cudaSuccess &&
-            dispatch_energy(ctx, grid, partial, dphi, derr) == cudaSuccess &&
+  bool ok = cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
+            dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                             ctx->stream) == cudaSuccess &&
             cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess;
+  if (ok && dcnt)
+    ok = cudaMemcpyAsync(hcnt, dcnt, sizeof hcnt, cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess;
   if (ok && phi_out && !(flags & BHMC_DEVICE_PTRS))
     ok = cudaMemcpyAsync(phi_out, dphi, sizeof(double) * ctx->S.n_tot, cudaMemcpyDeviceToHost, ctx->stream) ==
          cudaSuccess;
@@ -613,7 +619,18 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   double s = 0.0;
   for (double v : h) s += v;
   if (E) *E = 0.5 * ctx->S.lB * s;
+  if (total) {
+    total->visited = (int64_t)hcnt[0];
+    total->accepted = (int64_t)hcnt[1];
+    total->pairs = (int64_t)hcnt[2];
+    total->mac_fp64 = 0;
+  }
   return BHMC_OK;
+}
+
+bhmc_status bhmc_energy_counters(bhmc_ctx* ctx, double* E, bhmc_counters* total) {
+  if (!E || !total) return BHMC_EINVAL;
+  return energy_impl(ctx, E, nullptr, 0, total);
 }
 
 bhmc_status bhmc_energy(bhmc_ctx* ctx, double* E) {

@@ -86,10 +86,11 @@ __device__ __forceinline__ Real lane_multipole(const SysDev& S, const float4& a,
 }
 
 // partial[warp] = sum over the warp's targets of q_j phi_{T\{j}}(r_j); phi (may
-// be null) receives every target's potential.
+// be null) receives every target's potential; cnt (may be null) accumulates the
+// interaction-list counters {visited, multipole, direct pairs} over all targets.
 template <int P, typename Real, int LAYOUT>
 __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, double* partial, double* phi,
-                                                int* err) {
+                                                int* err, unsigned long long* cnt) {
   __shared__ EnergyStack stk[4];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
   const int SC = S.C + 2;
   double wsum = 0.0;
   int errv = 0;
+  unsigned c_vis = 0, c_acc = 0, c_pairs = 0;
   for (int base = warp * 32; base < S.n_tot; base += nwarps * 32) {
     const int jj = base + lane;
     const bool valid = jj < S.n_tot;
@@ -144,7 +146,9 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
         a.z = __shfl_sync(FULL, ha.z, o);
         a.w = __shfl_sync(FULL, ha.w, o);
         const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-        if (key == 0ULL || b.y == 0) continue;  // empty slot of the root group / empty cluster
+        if (key == 0ULL) continue;  // empty slot of the root group
+        c_vis += in_om ? 1u : 0u;
+        if (b.y == 0) continue;     // empty cluster
         const int node = en.x + o;
         const int sh = 3 * (S.Dmax - key_depth(key));
         const bool self = (kj >> sh) == key;
@@ -164,7 +168,10 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
           else
             dir = true;
         }
-        if (mul) acc.add(lane_multipole<P, Real, LAYOUT>(S, a, node, x, hi, lo, self, q, hi, lo));
+        if (mul) {
+          acc.add(lane_multipole<P, Real, LAYOUT>(S, a, node, x, hi, lo, self, q, hi, lo));
+          ++c_acc;
+        }
         const unsigned mo = __ballot_sync(FULL, opn), mf = __ballot_sync(FULL, fdv);
         if (mo | mf) {
           if (top >= BHMC_ESTACK_ENTRIES) {
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
             const float4 sa = S.sA[node * SC + k];
             const float4 sb = S.sB[node * SC + k];
             if (dir && __float_as_int(sb.w) != j) {
+              ++c_pairs;
               if (sizeof(Real) == 4) {
                 const float dx = (sa.x - hi[0]) + (sb.x - lo[0]);
                 const float dy = (sa.y - hi[1]) + (sb.y - lo[1]);
@@ -207,6 +215,20 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
   if (lane == 0) {
     partial[warp] = wsum;
     if (errv) atomicCAS(err, 0, errv);
+  }
+  if (cnt) {
+    unsigned long long v0 = c_vis, v1 = c_acc, v2 = c_pairs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(FULL, v0, o);
+      v1 += __shfl_xor_sync(FULL, v1, o);
+      v2 += __shfl_xor_sync(FULL, v2, o);
+    }
+    if (lane == 0) {
+      atomicAdd(cnt, v0);
+      atomicAdd(cnt + 1, v1);
+      atomicAdd(cnt + 2, v2);
+    }
   }
 }
 

@@ -77,13 +77,13 @@ int batch_occupancy<BHMC_P>(const SysDev& S0, int warps) {
 
 template <>
 cudaError_t launch_energy<BHMC_P>(const SysDev& S, int warps, int grid, double* partial, double* phi,
-                                  int* err, cudaStream_t st) {
+                                  int* err, unsigned long long* cnt, cudaStream_t st) {
   if (S.prec == BHMC_PREC_F64)
-    k_energy<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
+    k_energy<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err, cnt);
   else if (S.layout == BHMC_LAYOUT_AOS)
-    k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
+    k_energy<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err, cnt);
   else
-    k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err);
+    k_energy<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(S, S.order, partial, phi, err, cnt);
   return cudaGetLastError();
 }
 

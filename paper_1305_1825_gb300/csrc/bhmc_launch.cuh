@@ -28,6 +28,7 @@ template <int P>
 int batch_occupancy(const SysDev& S0, int warps);
 template <int P>
 cudaError_t launch_energy(const SysDev& S, int warps, int grid, double* partial, double* phi, int* err,
+                          unsigned long long* cnt,
                           cudaStream_t st);
 
 template <int P>
@@ -50,7 +51,8 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
                                               const BatchArgs*, int*, bhmc_mc_stats*,            \
                                               cudaStream_t);                                     \
   template <> int batch_occupancy<P>(const SysDev&, int);                                    \
-  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, cudaStream_t); \
+  template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, unsigned long long*, \
+                                           cudaStream_t);                                                  \
   template <> cudaError_t launch_forces<P>(const SysDev&, int, double*, double*, double*, double*, double*, int*, \
                                            cudaStream_t);
 

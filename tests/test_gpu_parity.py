@@ -213,3 +213,20 @@ def test_full_energy(bh, oracle_mod):
             assert abs(e_tree - e_ref) <= tol * abs(e_ref) + tol * scale
             # FP64 sums of N^2/2 mixed-sign pairs in different orders
             assert ctx.energy_direct() == pytest.approx(ref.energy_direct(), rel=1e-9)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_energy_counters_match_oracle(bh, oracle_mod, precision):
+    """The full-energy pass's interaction lists, summed over all targets, equal
+    the oracle's per-target traversals (target j excluded)."""
+    wl = W.colloid(n=600, seed=12)
+    ctx = bh.Context(wl, precision=precision, warps=2)
+    ref = _oracle(oracle_mod, wl)
+    E, cnt = ctx.energy_counters()
+    assert E == ctx.energy()
+    q, x = ref.charges()
+    want = np.zeros(3, dtype=np.int64)
+    for j in range(len(q)):
+        e = ref.phi(x[j], excl=[j])
+        want += (e.visited, e.accepted, e.pairs)
+    assert (cnt.visited, cnt.accepted, cnt.pairs) == tuple(int(v) for v in want)
