@@ -107,10 +107,77 @@ static bhmc_status validate(const bhmc_params* P) {
   if (P->images && !(P->image_R > 0.0)) return BHMC_EINVAL;
   if (P->precision != BHMC_PREC_F32 && P->precision != BHMC_PREC_F64) return BHMC_EINVAL;
   if (P->layout != BHMC_LAYOUT_SOA && P->layout != BHMC_LAYOUT_AOS) return BHMC_EINVAL;
-  if (P->warps != 1 && P->warps != 2 && P->warps != 4 && P->warps != 8) return BHMC_EINVAL;
+  if ((P->warps != 1 && P->warps != 2 && P->warps != 4 && P->warps != 8 && P->warps != 12 && P->warps != 16) ||
+      P->warps > BHMC_MAX_WARPS)
+    return BHMC_EINVAL;
   if (P->node_factor < 0.0) return BHMC_EINVAL;
   return BHMC_OK;
 }
+
+// Map from moments to evaluation coefficients: multiplying the recurrence of
+// Sec. 3.1 for T_n by r^(2k+1) gives polynomials N_n(R) = r^(2k+1) T_n(R),
+//   N_0 = 1,  N_n = -[(2k - 1) sum_i R_i N_{n - e_i} + (k - 1) r^2 sum_i N_{n - 2 e_i}] / k,
+// homogeneous of degree k; c(n, m) is the coefficient of R^m in N_n.
+struct WMap {
+  std::vector<int> row, col;
+  std::vector<float> val;
+};
+static WMap wmap_make(int p) {
+  const int K = nterms(p);
+  std::vector<std::vector<double>> N(K, std::vector<double>(K, 0.0));
+  std::vector<int> e1(K), e2(K), e3(K);
+  for (int k = 0; k <= p; ++k)
+    for (int n1 = k; n1 >= 0; --n1)
+      for (int n2 = k - n1; n2 >= 0; --n2) {
+        const int t = tidx(n1, n2, k - n1 - n2);
+        e1[t] = n1;
+        e2[t] = n2;
+        e3[t] = k - n1 - n2;
+      }
+  N[0][0] = 1.0;
+  for (int t = 1; t < K; ++t) {
+    const int n[3] = {e1[t], e2[t], e3[t]};
+    const int k = n[0] + n[1] + n[2];
+    for (int i = 0; i < 3; ++i) {
+      if (n[i] >= 1) {  // (2k - 1) R_i N_{n - e_i}
+        int m[3] = {n[0], n[1], n[2]};
+        m[i] -= 1;
+        const int s = tidx(m[0], m[1], m[2]);
+        for (int u = 0; u < K; ++u) {
+          if (N[s][u] == 0.0) continue;
+          int v[3] = {e1[u], e2[u], e3[u]};
+          v[i] += 1;
+          N[t][tidx(v[0], v[1], v[2])] -= (2.0 * k - 1.0) * N[s][u] / k;
+        }
+      }
+      if (n[i] >= 2) {  // (k - 1) r^2 N_{n - 2 e_i}
+        int m[3] = {n[0], n[1], n[2]};
+        m[i] -= 2;
+        const int s = tidx(m[0], m[1], m[2]);
+        for (int u = 0; u < K; ++u) {
+          if (N[s][u] == 0.0) continue;
+          for (int j = 0; j < 3; ++j) {
+            int v[3] = {e1[u], e2[u], e3[u]};
+            v[j] += 2;
+            N[t][tidx(v[0], v[1], v[2])] -= (k - 1.0) * N[s][u] / k;
+          }
+        }
+      }
+    }
+  }
+  WMap w;
+  w.row.push_back(0);
+  for (int m = 0; m < K; ++m) {
+    for (int n = 0; n < K; ++n)
+      if (N[n][m] != 0.0) {
+        w.col.push_back(n);
+        w.val.push_back((float)N[n][m]);
+      }
+    w.row.push_back((int)w.col.size());
+  }
+  return w;
+}
+static int wmap_nnz(int p) { return (int)wmap_make(p).col.size(); }
 
 template <typename T>
 static T* carve(char*& cur, size_t n) {
@@ -129,7 +196,11 @@ static size_t arena_bytes(const SysDev& S) {
   add(sizeof(float4) * S.node_cap);
   add(sizeof(int4) * S.node_cap);
   add(sizeof(float) * (size_t)S.node_cap * S.Kp);
+  add(sizeof(float) * (size_t)S.node_cap * S.Kp);
   add(sizeof(double) * (size_t)S.node_cap * S.K);
+  add(sizeof(int) * (S.K + 1));
+  add(sizeof(int) * wmap_nnz(S.p));
+  add(sizeof(float) * wmap_nnz(S.p));
   add(2 * sizeof(float4) * (size_t)S.node_cap * (S.C + 2));
   add(sizeof(int) * 2);
   add(sizeof(int) * S.group_cap);
@@ -151,7 +222,11 @@ static void carve_all(SysDev& S, char* base) {
   S.nA = carve<float4>(cur, S.node_cap);
   S.nB = carve<int4>(cur, S.node_cap);
   S.M32 = carve<float>(cur, (size_t)S.node_cap * S.Kp);
+  S.W32 = carve<float>(cur, (size_t)S.node_cap * S.Kp);
   S.M64 = carve<double>(cur, (size_t)S.node_cap * S.K);
+  S.wrow = carve<int>(cur, S.K + 1);
+  S.wcol = carve<int>(cur, wmap_nnz(S.p));
+  S.wval = carve<float>(cur, wmap_nnz(S.p));
   S.sA = carve<float4>(cur, (size_t)S.node_cap * (S.C + 2));
   S.sB = carve<float4>(cur, (size_t)S.node_cap * (S.C + 2));
   S.pool = carve<int>(cur, 2);
@@ -189,6 +264,9 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.rmin = P->shell_rmin;
   S.rmax = P->shell_rmax;
   S.img_R = P->image_R;
+  S.rmin2 = S.rmin * S.rmin;
+  S.rmax2 = S.rmax * S.rmax;
+  S.img_R2 = S.img_R * S.img_R;
   S.img_alpha = P->image_alpha;
   const double f = P->node_factor > 0.0 ? P->node_factor : (1.0 + std::max(1.0, 8.0 / P->C));
   long long cap = 64 + (long long)std::ceil(f * (double)S.n_tot);
@@ -340,6 +418,15 @@ static bhmc_status ctx_alloc(bhmc_ctx* c) {
   const size_t bytes = arena_bytes(c->S);
   if (cudaMalloc(&c->arena, bytes) != cudaSuccess) return BHMC_ENOMEM;
   carve_all(c->S, static_cast<char*>(c->arena));
+  const WMap w = wmap_make(c->S.p);
+  if (cudaMemcpyAsync(c->S.wrow, w.row.data(), sizeof(int) * w.row.size(), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->S.wcol, w.col.data(), sizeof(int) * w.col.size(), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->S.wval, w.val.data(), sizeof(float) * w.val.size(), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return BHMC_ECUDA;
   if (cudaMalloc(&c->io, sizeof(IoBlock)) != cudaSuccess) return BHMC_ENOMEM;
   if (cudaMallocHost(&c->io_host, sizeof(IoBlock)) != cudaSuccess) return BHMC_ENOMEM;
   return BHMC_OK;
@@ -600,7 +687,9 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   }
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
-  bool ok = cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
+  // the FP32 pass evaluates from W32, refreshed here from the running moments
+  bool ok = (ctx->S.prec != BHMC_PREC_F32 || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
+            cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
             dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                             ctx->stream) == cudaSuccess &&

@@ -73,13 +73,68 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   const int lg = 31 - __clz(cp);
   const int SC = S.C + 2;
   int top = 0, npop = 1;
-  uint2 e = make_uint2(0u, g == 0 ? pmask : 0u);
+  // A stack entry is a group of eight sibling clusters: {first node, bits 0-3
+  // points still traversing, bits 4-7 points summing directly, bits 8-11
+  // points whose own cluster is the group's parent, bits 12-16 depth}.
+  unsigned pm0 = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) pm0 |= T.pkey[s] != 0ULL ? (1u << s) : 0u;
+  uint2 e = make_uint2(0u, g == 0 ? (pmask | (pm0 << 8)) : 0u);
   int4 b = make_int4(-1, 0, 0, 0);
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (g == 0) {
     b = ld_int4(S.nB + (tid & 7));
     a = ld_float4(S.nA + (tid & 7));
   }
+  // Multipole and direct terms of one round's item lists; the first direct
+  // pass's slot loads are issued before the multipole work.
+  auto run_items = [&](int tm_, int td_) {
+    const int per = nth >> lg;
+    const int kk = tid & (cp - 1);
+    uint2 di0 = make_uint2(0u, 0u);
+    float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
+    bool have0 = false;
+    if ((tid >> lg) < td_) {
+      di0 = B.di[tid >> lg];
+      if (kk < (int)(di0.y >> 4)) {
+        const int slot = (int)di0.x * SC + kk;
+        sa0 = S.sA[slot];
+        sb0 = S.sB[slot];
+        have0 = true;
+      }
+    }
+    for (int k = tid; k < tm_; k += nth) {
+      const unsigned it = B.mi[k];
+      const int s = (int)(it & 3u);
+      if (GRAD) {
+        Real v, g0, g1, g2;
+        eval_item_grad<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u, v, g0, g1, g2);
+        ga.add(s, v, g0, g1, g2);
+      } else {
+        const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
+        acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
+      }
+    }
+    if (have0) {
+      if (GRAD)
+        direct_slot_grad<Real>(S, T, sa0, sb0, di0.y & 15u, ga, pairs);
+      else
+        direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
+    }
+    for (int base = per; base < td_; base += per) {
+      const int item = base + (tid >> lg);
+      if (item < td_) {
+        const uint2 di = B.di[item];
+        if (kk < (int)(di.y >> 4)) {
+          const int slot = (int)di.x * SC + kk;
+          if (GRAD)
+            direct_slot_grad<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, ga, pairs);
+          else
+            direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
+        }
+      }
+    }
+  };
   int rounds = 0;
   while (npop > 0) {
     if (++rounds > (1 << 22)) {
@@ -87,24 +142,36 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       break;
     }
     const int node = (int)e.x + (tid & 7);
-    const unsigned om = e.y & 15u, fd = (e.y >> 4) & 15u;
-    unsigned mac = 0, open = 0, fdc = 0, dir = 0, emask = 0;
+    const unsigned om = e.y & 15u, fd = (e.y >> 4) & 15u, pmp = (e.y >> 8) & 15u;
+    const int d = (int)(e.y >> 12);
+    unsigned mac = 0, open = 0, fdc = 0, dir = 0, emask = 0, onp = 0;
     int fc = -1, cnt = 0;
     const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
     if (g < npop && (om | fd) && key != 0ULL) {
       fc = b.x;
       cnt = b.y;
-      const int d = key_depth(key);
-      const int sh = 3 * (S.Dmax - d);
-      for (int k = 0; k < T.n_excl; ++k) emask |= ((T.ekey[k] >> sh) == key) ? (1u << k) : 0u;
-      if (path) {
-        const unsigned all = om | fd;
+      // points inside this cluster: those inside the parent whose octant at
+      // this depth is this cluster's (the root holds every point in the cube)
+      if (pmp) {
+        if (d == 0) {
+          onp = pmp;
+        } else {
+          const int sh = 3 * (S.Dmax - d);
+          const unsigned o = (unsigned)(tid & 7);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (((all >> s) & 1u) && (T.pkey[s] >> sh) == key) {
-            path[s][d] = node;
-            if (fc < 0) leafcnt[s] = cnt;
-          }
+          for (int s = 0; s < 4; ++s)
+            if (((pmp >> s) & 1u) && (unsigned)((T.pkey[s] >> sh) & 7ULL) == o) onp |= 1u << s;
+        }
+      }
+      // the excluded charges are the ion and its image at points 0 and 2
+      emask = (onp & 1u) | (T.n_excl > 1 ? ((onp >> 1) & 2u) : 0u);
+      if (path) {
+        unsigned pr = onp & (om | fd);
+        while (pr) {
+          const int s = __ffs(pr) - 1;
+          pr &= pr - 1;
+          path[s][d] = node;
+          if (fc < 0) leafcnt[s] = cnt;
         }
       }
       visited += __popc(om);
@@ -191,7 +258,9 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       err = BHMC_ESTACK;
       break;
     }
-    if (push) B.stk[top + op + __popc(pb & lt)] = make_uint2((unsigned)fc, open | (fdc << 4));
+    if (push)
+      B.stk[top + op + __popc(pb & lt)] =
+          make_uint2((unsigned)fc, open | (fdc << 4) | (onp << 8) | ((unsigned)(d + 1) << 12));
     {
       int pos = oi + incl - nm;
       unsigned m = mac;
@@ -217,52 +286,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       a_n = ld_float4(S.nA + nn);
     }
     top -= npop_n;
-    // first direct pass: issue its loads before the multipole work
-    const int per = nth >> lg;
-    const int kk = tid & (cp - 1);
-    uint2 di0 = make_uint2(0u, 0u);
-    float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
-    bool have0 = false;
-    if ((tid >> lg) < td) {
-      di0 = B.di[tid >> lg];
-      if (kk < (int)(di0.y >> 4)) {
-        const int slot = (int)di0.x * SC + kk;
-        sa0 = S.sA[slot];
-        sb0 = S.sB[slot];
-        have0 = true;
-      }
-    }
-    for (int k = tid; k < tm; k += nth) {
-      const unsigned it = B.mi[k];
-      const int s = (int)(it & 3u);
-      if (GRAD) {
-        Real v, g0, g1, g2;
-        eval_item_grad<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u, v, g0, g1, g2);
-        ga.add(s, v, g0, g1, g2);
-      } else {
-        const Real v = eval_item<P, Real, LAYOUT>(S, T, (int)(it >> 4), s, (it >> 2) & 3u);
-        acc.add(sizeof(Real) == 4 ? (Real)(T.w[s] * (float)v) : (Real)(T.w64[s] * (double)v));
-      }
-    }
-    if (have0) {
-      if (GRAD)
-        direct_slot_grad<Real>(S, T, sa0, sb0, di0.y & 15u, ga, pairs);
-      else
-        direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
-    }
-    for (int base = per; base < td; base += per) {
-      const int item = base + (tid >> lg);
-      if (item < td) {
-        const uint2 di = B.di[item];
-        if (kk < (int)(di.y >> 4)) {
-          const int slot = (int)di.x * SC + kk;
-          if (GRAD)
-            direct_slot_grad<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, ga, pairs);
-          else
-            direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
-        }
-      }
-    }
+    run_items(tm, td);
     // No barrier here: the next round writes the stack, the item lists and the
     // per-warp counts only after its first barrier, which every thread reaches
     // after finishing this round's items.

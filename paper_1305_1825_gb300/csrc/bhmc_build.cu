@@ -244,6 +244,18 @@ __global__ void k_moments_m2m(SysDev S, int node_begin, int node_end) {
   }
 }
 
+// Evaluation coefficients of every cluster in use (FP32 traversal).
+__global__ void k_wmirror(SysDev S, int n_nodes) {
+  const long long total = (long long)n_nodes * S.K;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int nd = (int)(it / S.K), t = (int)(it - (long long)nd * S.K);
+    const int4 b = S.nB[nd];
+    if (b.z == 0 && b.w == 0) continue;
+    w_store(S, nd, t);
+  }
+}
+
 // Stand-alone local adjustment (bhmc_commit_move): paths by descent from the root.
 __global__ void __launch_bounds__(256) k_commit(SysDev S, int i, double bx, double by, double bz, int* status) {
   __shared__ MoveStore st;
@@ -353,6 +365,10 @@ cudaError_t build_leaves_moments(const SysDev& S, int n_nodes, const int* perm, 
     const int b = level_begin[d], e = level_begin[d + 1];
     k_moments_m2m<<<grid_for((long long)(e - b) * S.K, 256), 256, 0, st>>>(S, b, e);
   }
+  return cudaGetLastError();
+}
+cudaError_t launch_wmirror(const SysDev& S, cudaStream_t st) {
+  k_wmirror<<<grid_for((long long)S.node_cap * S.K, 256), 256, 0, st>>>(S, S.node_cap);
   return cudaGetLastError();
 }
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st) {

@@ -9,7 +9,9 @@
 
 #define BHMC_MAX_P 6
 #define BHMC_MAX_D 20
+#ifndef BHMC_MAX_WARPS
 #define BHMC_MAX_WARPS 8
+#endif
 #define BHMC_ENERGY_WARPS 4
 #define BHMC_MAX_C 32
 
@@ -39,7 +41,9 @@ struct SysDev {
   double inv_hmin;          // 2^Dmax / side (a power of two)
   long long root_cell[3];   // root_lo * inv_hmin (integers)
   double rmin, rmax;        // shell radii
+  double rmin2, rmax2;      // rmin * rmin, rmax * rmax (FP64 products)
   double img_R, img_alpha;
+  double img_R2;            // img_R * img_R
   // charges
   double *px, *py, *pz, *pq;
   unsigned long long* ckey;
@@ -52,6 +56,13 @@ struct SysDev {
   int4* nB;
   float* M32;   // SoA [K][node_cap] or AoS [node_cap][Kp]
   double* M64;  // [node_cap][K]
+  // Evaluation coefficients W_m = sum_n c(n, m) M_n with r^(2k+1) T_n(R) =
+  // sum_{|m| = k} c(n, m) R^m, so that sum_{|n| = k} T_n(R) M_n =
+  // r^-(2k+1) sum_{|m| = k} W_m R^m (FP32, laid out like M32; FP32 traversal)
+  float* W32;
+  int* wrow;    // CSR of the map by output term: wrow[K + 1], wcol/wval[nnz]
+  int* wcol;
+  float* wval;
   float4* sA;
   float4* sB;
   int* pool;    // pool[0] = next unused group, pool[1] = number of free groups
@@ -121,7 +132,7 @@ __device__ __forceinline__ bool image_of(const SysDev& S, const double r[3], dou
                         __dmul_rn(r[2], r[2]));
   if (!(r2 > 0.0)) return false;
   double rn = __dsqrt_rn(r2);
-  double f = __ddiv_rn(__dmul_rn(S.img_R, S.img_R), r2);
+  double f = __ddiv_rn(S.img_R2, r2);
   out[0] = __dmul_rn(f, r[0]);
   out[1] = __dmul_rn(f, r[1]);
   out[2] = __dmul_rn(f, r[2]);
@@ -142,7 +153,7 @@ __device__ __forceinline__ bool shell_ok(const SysDev& S, const double x[3]) {
   if (!S.shell) return true;
   double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])),
                         __dmul_rn(x[2], x[2]));
-  return r2 >= __dmul_rn(S.rmin, S.rmin) && r2 <= __dmul_rn(S.rmax, S.rmax);
+  return r2 >= S.rmin2 && r2 <= S.rmax2;
 }
 
 __device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S.err, 0, code); }
@@ -172,6 +183,14 @@ __device__ __forceinline__ double mono_term(int n1, int n2, int n3, double q, do
 
 __device__ __forceinline__ int m32_index(const SysDev& S, int node, int t) {
   return S.layout == BHMC_LAYOUT_SOA ? t * S.node_cap + node : node * S.Kp + t;
+}
+
+// Evaluation coefficient W_t of a cluster from its FP64 moments (FP32 sums).
+__device__ __forceinline__ void w_store(const SysDev& S, int node, int t) {
+  const double* M = S.M64 + (size_t)node * S.K;
+  float w = 0.f;
+  for (int j = S.wrow[t]; j < S.wrow[t + 1]; ++j) w = fmaf(S.wval[j], __double2float_rn(M[S.wcol[j]]), w);
+  S.W32[m32_index(S, node, t)] = w;
 }
 
 }  // namespace bhmc

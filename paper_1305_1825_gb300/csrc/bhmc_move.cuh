@@ -55,66 +55,130 @@ __device__ __forceinline__ void init_tables(MoveSh& sh, int K) {
   }
 }
 
+// Role r of the setup runs on warp r when the block has it, else on lanes
+// 8r..8r+7 of warp 0; k is the lane within the role.
+__device__ __forceinline__ bool setup_role(int r, int& k, int& base) {
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = W > r ? r : 0;
+  base = W > r ? 0 : 8 * r;
+  k = lane - base;
+  return warp == w && k >= 0 && k < 8;
+}
+
+// Lanes base..base+2 hold coordinate k of a point x: the depth-Dmax key of x
+// (0 outside the root cube, as point_key) in every lane, and
+// r2 = (x0*x0 + x1*x1) + x2*x2 in every lane (FP64, the order of the definition).
+__device__ __forceinline__ unsigned long long lane_key(const SysDev& S, double xk, int k, int base,
+                                                       unsigned m3) {
+  const double lim = (double)(1LL << S.Dmax);
+  const double f = floor(__dmul_rn(xk, S.inv_hmin)) - (double)S.root_cell[k];
+  const bool ok = f >= 0.0 && f < lim;
+  unsigned long long c = ok ? (spread3((unsigned long long)(long long)f) << k) : 0ULL;
+  const unsigned okm = __ballot_sync(m3, ok);
+  c |= __shfl_sync(m3, c, base + 1) | __shfl_sync(m3, c, base + 2);
+  c = __shfl_sync(m3, c, base);
+  return ((okm >> base) & 7u) == 7u ? ((1ULL << (3 * S.Dmax)) | c) : 0ULL;
+}
+__device__ __forceinline__ double lane_r2(double xk, int base, unsigned m3) {
+  const double sq = __dmul_rn(xk, xk);
+  const double s1 = __shfl_sync(m3, sq, base + 1), s2 = __shfl_sync(m3, sq, base + 2);
+  const double s0 = __shfl_sync(m3, sq, base);
+  return __dadd_rn(__dadd_rn(s0, s1), s2);
+}
+
 // ---------------------------------------------------------------------------
 // Set up the move of ion sh.i to sh.b (all threads; sh.i and sh.b written
-// before a barrier).  The ion's and the image's FP64 work run on different
-// warps.  Sets sh.outcome = -1 to proceed or the rejection outcome, with the
+// before a barrier).  FP64 is slow on this part, so its work is spread over
+// lanes (x, y, z side by side) and warps: role 0 the ion and the trial point's
+// key and shell test, role 1 the trial image and its key, role 2 the image
+// charge.  Sets sh.outcome = -1 to proceed or the rejection outcome, with the
 // tests in the oracle's order: root cube, shell, image, image in root cube.
 static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
   TravPts& T = sh.T;
   const int i = sh.i;
-  const int img_tid = W > 1 ? 32 : 1;
-  if (tid == 0) {
-    sh.q = S.pq[i];
-    sh.a[0] = S.px[i];
-    sh.a[1] = S.py[i];
-    sh.a[2] = S.pz[i];
-    const unsigned long long k = S.ckey[i];
-    T.pkey[0] = k;
-    T.ekey[0] = k;
-    T.pkey[1] = point_key(S, sh.b[0], sh.b[1], sh.b[2]);
-    sh.rej_dom = T.pkey[1] == 0ULL;  // outside the root cube
-    sh.rej_shell = !shell_ok(S, sh.b);
-    sh.npts = S.images ? 4 : 2;
-    sh.nmov = S.images ? 2 : 1;
-    T.n_excl = sh.nmov;
-    T.excl[0] = i;
-  } else if (tid == img_tid) {
-    sh.rej_img = 0;
-    sh.qa_img = 0.0;
-    sh.qb_img = 0.0;
-    if (S.images) {
-      const int img = S.n_mob + S.n_fix + i;
-      sh.img = img;
-      T.excl[1] = img;
-      sh.ai[0] = S.px[img];
-      sh.ai[1] = S.py[img];
-      sh.ai[2] = S.pz[img];
-      sh.qa_img = S.pq[img];
-      const unsigned long long k = S.ckey[img];
-      T.pkey[2] = k;
-      T.ekey[1] = k;
-      double bi[3], qb;
-      unsigned long long kb = 0ULL;
-      if (image_of(S, sh.b, S.pq[i], bi, &qb)) kb = point_key(S, bi[0], bi[1], bi[2]);
-      if (kb == 0ULL) {
-        sh.rej_img = 1;
-        bi[0] = bi[1] = bi[2] = 0.0;
-        qb = 0.0;
+  int k, base;
+  if (setup_role(0, k, base)) {
+    const unsigned m3 = 7u << base;
+    if (k < 3) {
+      const double bk = sh.b[k];
+      const unsigned long long kb = lane_key(S, bk, k, base, m3);
+      const double r2 = lane_r2(bk, base, m3);
+      if (k == 0) {
+        T.pkey[1] = kb;
+        sh.rej_dom = kb == 0ULL;  // outside the root cube
+        sh.rej_shell = S.shell ? !(r2 >= S.rmin2 && r2 <= S.rmax2) : 0;
+        sh.npts = S.images ? 4 : 2;
+        sh.nmov = S.images ? 2 : 1;
+        T.n_excl = sh.nmov;
+        T.excl[0] = i;
       }
-      sh.bi[0] = bi[0];
-      sh.bi[1] = bi[1];
-      sh.bi[2] = bi[2];
-      sh.qb_img = qb;
-      T.pkey[3] = kb;
+    } else if (k == 3) {
+      sh.q = S.pq[i];
+    } else if (k == 4) {
+      const unsigned long long ck = S.ckey[i];
+      T.pkey[0] = ck;
+      T.ekey[0] = ck;
+    } else {
+      sh.a[k - 5] = (k == 5 ? S.px : (k == 6 ? S.py : S.pz))[i];
+    }
+  }
+  if (setup_role(1, k, base)) {
+    const unsigned m3 = 7u << base;
+    if (!S.images) {
+      if (k == 0) {
+        sh.rej_img = 0;
+        sh.qa_img = 0.0;
+      }
+    } else if (k < 3) {
+      const double bk = sh.b[k];
+      const double r2 = lane_r2(bk, base, m3);
+      double bik = 0.0;
+      unsigned long long kb = 0ULL;
+      if (r2 > 0.0) {
+        bik = __dmul_rn(__ddiv_rn(S.img_R2, r2), bk);
+        kb = lane_key(S, bik, k, base, m3);
+      }
+      sh.bi[k] = kb ? bik : 0.0;
+      if (k == 0) {
+        T.pkey[3] = kb;
+        sh.rej_img = kb == 0ULL;
+      }
+    } else {
+      const int img = S.n_mob + S.n_fix + i;
+      if (k == 3) {
+        sh.img = img;
+        T.excl[1] = img;
+        sh.qa_img = S.pq[img];
+      } else if (k == 4) {
+        const unsigned long long ck = S.ckey[img];
+        T.pkey[2] = ck;
+        T.ekey[1] = ck;
+      } else {
+        sh.ai[k - 5] = (k == 5 ? S.px : (k == 6 ? S.py : S.pz))[img];
+      }
+    }
+  }
+  if (setup_role(2, k, base)) {
+    const unsigned m3 = 7u << base;
+    if (!S.images) {
+      if (k == 0) sh.qb_img = 0.0;
+    } else if (k < 3) {
+      const double r2 = lane_r2(sh.b[k], base, m3);
+      if (k == 0) {
+        double qb = 0.0;
+        if (r2 > 0.0) qb = __ddiv_rn(__dmul_rn(__dmul_rn(S.img_alpha, S.pq[i]), S.img_R), __dsqrt_rn(r2));
+        sh.qb_img = qb;
+      }
     }
   }
   __syncthreads();
   if (warp == 0) {
-    if (lane == 0)
+    if (lane == 0) {
       sh.outcome = sh.rej_dom ? BHMC_REJECT_DOMAIN
                               : sh.rej_shell ? BHMC_REJECT_OVERLAP : sh.rej_img ? BHMC_REJECT_DOMAIN : -1;
+      if (sh.rej_img) sh.qb_img = 0.0;
+    }
     if (lane < 3 * sh.npts) {
       const int s = lane / 3, k = lane - 3 * (lane / 3);
       const double* pts[4] = {sh.a, sh.b, sh.ai, sh.bi};
@@ -573,21 +637,26 @@ template <int P, typename Real, int LAYOUT>
 __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica,
                        uint2 key, double step, MoveRec* rec) {
   MoveSh& sh = st.sh;
-  if (threadIdx.x == 0) {
-    const uint4 u = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 0u), key);
-    const uint4 v = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, 1u), key);
-    const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
-    const unsigned uu[3] = {u.y, u.z, u.w};
-    const double src[3] = {S.px[i], S.py[i], S.pz[i]};
-    for (int k = 0; k < 3; ++k) {
+  if (threadIdx.x < 4) {
+    // lanes 0-2: coordinate k of the trial position from block (m, replica, 0);
+    // lane 3: alpha from block (m, replica, 1)
+    const int k = threadIdx.x;
+    const uint4 u = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, k < 3 ? 0u : 1u), key);
+    if (k < 3) {
+      const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
+      const unsigned uk = k == 0 ? u.y : (k == 1 ? u.z : u.w);
+      const double src = (k == 0 ? S.px : (k == 1 ? S.py : S.pz))[i];
       const double delta =
-          __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)uu[k], 0x1p-32), 0x1p-33), 0.5), step);
-      sh.b[k] = __dadd_rn(src[k], delta);
+          __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)uk, 0x1p-32), 0x1p-33), 0.5), step);
+      sh.b[k] = __dadd_rn(src, delta);
+      if (k == 0) {
+        sh.i = i;
+        sh.dE = 0.0;
+        sh.flagged = 0;
+      }
+    } else {
+      sh.alpha = __dmul_rn(__dadd_rn((double)u.x, 0.5), 0x1p-32);
     }
-    sh.i = i;
-    sh.dE = 0.0;
-    sh.flagged = 0;
-    sh.alpha = __dmul_rn(__dadd_rn((double)v.x, 0.5), 0x1p-32);
   }
   __syncthreads();
   setup_move(S, sh);
@@ -793,7 +862,7 @@ struct DeltaOut {
 };
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(256) k_delta(SysDev S, int i, double bx, double by, double bz,
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_delta(SysDev S, int i, double bx, double by, double bz,
                                                DeltaOut* out) {
   __shared__ MoveStore st;
   if (threadIdx.x == 0) {
@@ -819,7 +888,7 @@ __global__ void __launch_bounds__(256) k_delta(SysDev S, int i, double bx, doubl
 }
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(256) k_step(SysDev S, unsigned long long m, unsigned replica,
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step(SysDev S, unsigned long long m, unsigned replica,
                                               uint2 key, double step, MoveRec* recs,
                                               bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
@@ -833,7 +902,7 @@ __global__ void __launch_bounds__(256) k_step(SysDev S, unsigned long long m, un
 }
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(256) k_step_mala(SysDev S, unsigned long long m, unsigned replica, uint2 key,
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step_mala(SysDev S, unsigned long long m, unsigned replica, uint2 key,
                                                    double tau, MoveRec* recs, bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   if (*(volatile int*)S.err) return;
@@ -852,7 +921,7 @@ struct BatchArgs {
 };
 
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(256) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
                                                int* next, bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   __shared__ int rep;

@@ -197,6 +197,78 @@ __device__ __forceinline__ void eval_item_grad(const SysDev& S, const TravPts& T
   }
 }
 
+// FP32 multipole sum_{|n| <= p} T_n(R) M_n of cluster `node` from its
+// evaluation coefficients: with u = R / r, sum_{|n| = k} T_n(R) M_n =
+// r^-(k+1) sum_{|m| = k} W_m u^m, so the sum is r^-1 (P_0 + r^-1 (P_1 + ...)).
+// Each of the `ne` charges (qe, offset d from the cluster centre) is removed
+// through its own truncated expansion, sum_{|n| = k} T_n(R) d^n =
+// (-1)^k Q_k r^-(k+1) with Q_0 = 1, Q_1 = u.d, Q_{k+1} = ((2k+1)(u.d) Q_k -
+// k |d|^2 Q_{k-1}) / (k+1) (the Legendre recurrence; 1/|R + d| = sum_k
+// (-1)^k |d|^k P_k(cos) / r^(k+1)).
+template <int P, int LAYOUT>
+__device__ __forceinline__ float w_multipole(const SysDev& S, int node, float rx, float ry, float rz, int ne,
+                                             const float* qe, const float (*de)[3]) {
+  constexpr int K = nterms(P), KP = pad4(K);
+  float W[KP];
+  if (LAYOUT == BHMC_LAYOUT_AOS) {
+    const float4* W4 = reinterpret_cast<const float4*>(S.W32 + (size_t)node * KP);
+#pragma unroll
+    for (int t4 = 0; t4 < KP / 4; ++t4) {
+      const float4 v = W4[t4];
+      W[4 * t4] = v.x;
+      W[4 * t4 + 1] = v.y;
+      W[4 * t4 + 2] = v.z;
+      W[4 * t4 + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < K; ++t) W[t] = S.W32[(size_t)t * S.node_cap + node];
+  }
+  const float rinv = rsqrtf(rx * rx + ry * ry + rz * rz);
+  const float ux = rx * rinv, uy = ry * rinv, uz = rz * rinv;
+  float px[P + 1], py[P + 1], pz[P + 1];
+  px[0] = py[0] = pz[0] = 1.f;
+#pragma unroll
+  for (int k = 1; k <= P; ++k) {
+    px[k] = px[k - 1] * ux;
+    py[k] = py[k - 1] * uy;
+    pz[k] = pz[k - 1] * uz;
+  }
+  float pk[P + 1];
+#pragma unroll
+  for (int k = 0; k <= P; ++k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int n1 = k; n1 >= 0; --n1) {
+      const float pxy0 = px[n1];
+#pragma unroll
+      for (int n2 = k - n1; n2 >= 0; --n2) {
+        const int n3 = k - n1 - n2;
+        acc = fmaf(W[tidx(n1, n2, n3)], (pxy0 * py[n2]) * pz[n3], acc);
+      }
+    }
+    pk[k] = acc;
+  }
+  for (int e = 0; e < ne; ++e) {
+    const float dx = de[e][0], dy = de[e][1], dz = de[e][2];
+    const float sd = ux * dx + uy * dy + uz * dz, td = dx * dx + dy * dy + dz * dz;
+    float q0 = 1.f, q1 = sd;
+    pk[0] -= qe[e];
+    if (P >= 1) pk[1] += qe[e] * q1;
+#pragma unroll
+    for (int k = 1; k < P; ++k) {
+      const float q2 = ((2.f * k + 1.f) * sd * q1 - (float)k * td * q0) * (1.f / (k + 1.f));
+      pk[k + 1] += ((k + 1) & 1) ? qe[e] * q2 : -qe[e] * q2;
+      q0 = q1;
+      q1 = q2;
+    }
+  }
+  float acc = pk[P];
+#pragma unroll
+  for (int k = P - 1; k >= 0; --k) acc = fmaf(acc, rinv, pk[k]);
+  return acc * rinv;
+}
+
 // Multipole term of cluster `node` at point s: sum_n T_n(r_A - x) M'_n with
 // M' = M minus the terms of the excluded charges inside the cluster (emask);
 // the excluded charges' own expansions are subtracted explicitly.
