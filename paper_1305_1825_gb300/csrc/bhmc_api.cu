@@ -42,6 +42,7 @@ struct bhmc_ctx {
   void* io_host = nullptr;  // pinned mirror
   int sticky = 0;
   bool borrowed = false;
+  bool w_stale = true;  // W32 not refreshed since the moments last changed
 };
 
 struct bhmc_batch {
@@ -102,6 +103,11 @@ static bhmc_status validate(const bhmc_params* P) {
     // every cluster centre must be exact in FP32: |centre| / (hmin/2) < 2^24
     const double far = (std::fabs(P->root_lo[a]) + P->root_side) / (0.5 * hmin);
     if (far >= 16777216.0) return BHMC_EINVAL;
+  }
+  {
+    int ex = 0;
+    std::frexp(P->root_side, &ex);
+    if (ex < -150 || ex > 150) return BHMC_EINVAL;  // keeps x * 2^Dmax / side exact for |x| >= 2^-823
   }
   if (P->shell && !(P->shell_rmin >= 0.0 && P->shell_rmax >= P->shell_rmin)) return BHMC_EINVAL;
   if (P->images && !(P->image_R > 0.0)) return BHMC_EINVAL;
@@ -257,6 +263,7 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.lBf = (float)P->lB;
   S.root_side = P->root_side;
   S.inv_hmin = std::ldexp(1.0, P->Dmax) / P->root_side;
+  S.hmin_shift = std::ilogb(S.inv_hmin);
   for (int a = 0; a < 3; ++a) {
     S.root_lo[a] = P->root_lo[a];
     S.root_cell[a] = (long long)(P->root_lo[a] * S.inv_hmin);
@@ -546,6 +553,7 @@ bhmc_status bhmc_delta_energy(bhmc_ctx* ctx, int64_t i, const double r_new[3], d
 bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
+  ctx->w_stale = true;
   if (i < 0 || i >= ctx->S.n_mob || !r_new) return BHMC_EINVAL;
   IoBlock* dio = static_cast<IoBlock*>(ctx->io);
   IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
@@ -569,6 +577,7 @@ bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t 
                          bhmc_mc_stats* stats, bhmc_move_record* records) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
+  ctx->w_stale = true;
   if (!stats || !(step >= 0.0)) return BHMC_EINVAL;
   if (n_moves > 0 && ctx->S.n_mob < 1) return BHMC_EINVAL;  // no mobile ion to move
   IoBlock* dio = static_cast<IoBlock*>(ctx->io);
@@ -600,6 +609,7 @@ bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t
                            bhmc_mc_stats* stats, bhmc_move_record* records) {
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
+  ctx->w_stale = true;
   if (!stats || !(tau > 0.0)) return BHMC_EINVAL;
   if (n_moves > 0 && ctx->S.n_mob < 1) return BHMC_EINVAL;
   IoBlock* dio = static_cast<IoBlock*>(ctx->io);
@@ -688,7 +698,7 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
   // the FP32 pass evaluates from W32, refreshed here from the running moments
-  bool ok = (ctx->S.prec != BHMC_PREC_F32 || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
+  bool ok = (ctx->S.prec != BHMC_PREC_F32 || !ctx->w_stale || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
             cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
             dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
@@ -705,6 +715,7 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   if (phi_out && !(flags & BHMC_DEVICE_PTRS)) cudaFree(dphi);
   if (!ok) return BHMC_ECUDA;
   if (herr) return (bhmc_status)herr;
+  ctx->w_stale = false;
   double s = 0.0;
   for (double v : h) s += v;
   if (E) *E = 0.5 * ctx->S.lB * s;
@@ -960,6 +971,8 @@ bhmc_status bhmc_batch_replica(bhmc_batch* B, int32_t r, bhmc_ctx** ctx) {
 
 bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
                                uint64_t move0, bhmc_mc_stats* stats) {
+  if (B)
+    for (bhmc_ctx* c : B->reps) c->w_stale = true;
   if (!B || !seeds || !(step >= 0.0)) return BHMC_EINVAL;
   const int n = (int)B->reps.size();
   for (bhmc_ctx* c : B->reps) {

@@ -79,12 +79,24 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   unsigned pm0 = 0;
 #pragma unroll
   for (int s = 0; s < 4; ++s) pm0 |= T.pkey[s] != 0ULL ? (1u << s) : 0u;
-  uint2 e = make_uint2(0u, g == 0 ? (pmask | (pm0 << 8)) : 0u);
+  // Every point lies in the root cube, so the root fails the MAC (rho^2 =
+  // 3h^2 > theta^2 d^2 for theta < 1); when it is internal with N' > N0 the
+  // walk starts from its children, and the root counts as visited.
+  const int4 rb = ld_int4(S.nB);
+  const bool skip_root = rb.x >= 0 && rb.y - T.n_excl > S.N0;
+  const int g0 = skip_root ? rb.x : 0;
+  uint2 e = make_uint2((unsigned)g0, g == 0 ? (pmask | (pm0 << 8) | (skip_root ? (1u << 12) : 0u)) : 0u);
+  if (skip_root && tid == 0) {
+    visited += __popc(pmask);
+    if (path)
+      for (int s = 0; s < 4; ++s)
+        if ((pmask >> s) & 1u) path[s][0] = 0;
+  }
   int4 b = make_int4(-1, 0, 0, 0);
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (g == 0) {
-    b = ld_int4(S.nB + (tid & 7));
-    a = ld_float4(S.nA + (tid & 7));
+    b = ld_int4(S.nB + g0 + (tid & 7));
+    a = ld_float4(S.nA + g0 + (tid & 7));
   }
   // Multipole and direct terms of one round's item lists; the first direct
   // pass's slot loads are issued before the multipole work.

@@ -39,6 +39,7 @@ struct SysDev {
   float theta2f, lBf;
   double root_lo[3], root_side;
   double inv_hmin;          // 2^Dmax / side (a power of two)
+  int hmin_shift;           // log2(inv_hmin)
   long long root_cell[3];   // root_lo * inv_hmin (integers)
   double rmin, rmax;        // shell radii
   double rmin2, rmax2;      // rmin * rmin, rmax * rmax (FP64 products)
@@ -104,15 +105,47 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
 
 // Returns 0 if the point is outside the root cube (NaN and infinities included:
 // the range test is done on the floored doubles before any integer conversion).
+// Cell index floor(x * inv_hmin) - root_cell[a] along axis a, and whether it
+// lies in [0, 2^Dmax).  inv_hmin = 2^s, so x * inv_hmin is exact and the floor
+// can be read from the bits of x; tiny |x| (exponent below 2^-823, where the
+// product could leave the normal range) takes the FP64 formula itself.
+__device__ __forceinline__ bool cell_of(const SysDev& S, double x, int a, long long& c) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  long long f;
+  if (e == 0x7ff) return false;  // NaN or infinity
+  if (e < 200) {
+    const double ff = floor(__dmul_rn(x, S.inv_hmin)) - (double)S.root_cell[a];
+    if (!(ff >= 0.0 && ff < (double)(1LL << S.Dmax))) return false;
+    c = (long long)ff;
+    return true;
+  }
+  const unsigned long long M = (u & 0xfffffffffffffULL) | (1ULL << 52);
+  const int sh = e - 1075 + S.hmin_shift;  // |x| * 2^s = M * 2^sh
+  if (sh >= 9) return false;                // |x| 2^s >= 2^61: outside the cube
+  long long v;
+  bool frac;
+  if (sh >= 0) {
+    v = (long long)(M << sh);
+    frac = false;
+  } else if (sh > -64) {
+    v = (long long)(M >> -sh);
+    frac = (M & ((1ULL << -sh) - 1ULL)) != 0ULL;
+  } else {
+    v = 0;
+    frac = true;
+  }
+  f = (u >> 63) ? -v - (frac ? 1 : 0) : v;
+  c = f - S.root_cell[a];
+  return c >= 0 && c < (1LL << S.Dmax);
+}
+
 __device__ __forceinline__ unsigned long long point_key(const SysDev& S, double x, double y,
                                                         double z) {
-  const double lim = (double)(1LL << S.Dmax);
-  const double fx = floor(__dmul_rn(x, S.inv_hmin)) - (double)S.root_cell[0];
-  const double fy = floor(__dmul_rn(y, S.inv_hmin)) - (double)S.root_cell[1];
-  const double fz = floor(__dmul_rn(z, S.inv_hmin)) - (double)S.root_cell[2];
-  if (!(fx >= 0.0 && fx < lim && fy >= 0.0 && fy < lim && fz >= 0.0 && fz < lim)) return 0ULL;
-  const long long kx = (long long)fx, ky = (long long)fy, kz = (long long)fz;
-  return (1ULL << (3 * S.Dmax)) | spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+  long long kx, ky, kz;
+  if (!cell_of(S, x, 0, kx) || !cell_of(S, y, 1, ky) || !cell_of(S, z, 2, kz)) return 0ULL;
+  return (1ULL << (3 * S.Dmax)) | spread3((unsigned long long)kx) | (spread3((unsigned long long)ky) << 1) |
+         (spread3((unsigned long long)kz) << 2);
 }
 
 __device__ __forceinline__ int key_depth(unsigned long long k) { return (63 - __clzll(k)) / 3; }

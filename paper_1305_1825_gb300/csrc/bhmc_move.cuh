@@ -12,27 +12,36 @@
 
 namespace bhmc {
 
-struct MoveSh {
+// State of one trial move produced by its setup: the proposal, the four
+// evaluation points and the rejection tests.
+struct MoveSetup {
   TravPts T;
   int i, img, npts, nmov;
   double q, qa_img, qb_img;
   double a[3], b[3], ai[3], bi[3];
+  int outcome, flagged;
+  int rej_dom, rej_shell, rej_img;
+  double dE, alpha;
+};
+
+struct MoveSh : MoveSetup {
   int path[4][BHMC_MAX_D + 1];
   int plen[4];
   int leafcnt[4];          // pre-move counts of the four path leaves
   int slot_i, slot_img;    // pre-move leaf slots of the ion and its image
   int merge_d[2];          // topmost level to merge on each old path
-  double part[BHMC_MAX_WARPS];
   int cnt[BHMC_MAX_WARPS][5];
-  int outcome, flagged, go;
-  int rej_dom, rej_shell, rej_img;
-  double dE, alpha;
+  int go;
   double xi[3];            // Langevin proposals: normal variates
   double U[2], gU[2][3];   // single-ion energy and gradient at the old / new position
   double tphi[2], tgrad[2][3];  // per-role potential and gradient of the last gradient traversal
   int split_node, split_g;
   unsigned char ex[nterms(BHMC_MAX_P)][3];  // exponents of every moment term
-  float4 tA[BHMC_MAX_C + 2], tB[BHMC_MAX_C + 2];
+  float4 tA[BHMC_MAX_C + 2], tB[BHMC_MAX_C + 2];  // leaf slots of a merge
+  // the next move's setup, computed while this move is decided, and its move
+  // index (~0: none)
+  MoveSetup nxt;
+  unsigned long long nxt_m;
 };
 
 struct MoveStore {
@@ -55,12 +64,12 @@ __device__ __forceinline__ void init_tables(MoveSh& sh, int K) {
   }
 }
 
-// Role r of the setup runs on warp r when the block has it, else on lanes
-// 8r..8r+7 of warp 0; k is the lane within the role.
-__device__ __forceinline__ bool setup_role(int r, int& k, int& base) {
+// Role r of the setup runs on warp wb + r when the block has it, else on
+// lanes 8r..8r+7 of warp wb; k is the lane within the role.
+__device__ __forceinline__ bool setup_role(int r, int wb, int& k, int& base) {
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = W > r ? r : 0;
-  base = W > r ? 0 : 8 * r;
+  const int w = W > wb + r ? wb + r : wb;
+  base = W > wb + r ? 0 : 8 * r;
   k = lane - base;
   return warp == w && k >= 0 && k < 8;
 }
@@ -70,10 +79,9 @@ __device__ __forceinline__ bool setup_role(int r, int& k, int& base) {
 // r2 = (x0*x0 + x1*x1) + x2*x2 in every lane (FP64, the order of the definition).
 __device__ __forceinline__ unsigned long long lane_key(const SysDev& S, double xk, int k, int base,
                                                        unsigned m3) {
-  const double lim = (double)(1LL << S.Dmax);
-  const double f = floor(__dmul_rn(xk, S.inv_hmin)) - (double)S.root_cell[k];
-  const bool ok = f >= 0.0 && f < lim;
-  unsigned long long c = ok ? (spread3((unsigned long long)(long long)f) << k) : 0ULL;
+  long long ck;
+  const bool ok = cell_of(S, xk, k, ck);
+  unsigned long long c = ok ? (spread3((unsigned long long)ck) << k) : 0ULL;
   const unsigned okm = __ballot_sync(m3, ok);
   c |= __shfl_sync(m3, c, base + 1) | __shfl_sync(m3, c, base + 2);
   c = __shfl_sync(m3, c, base);
@@ -86,20 +94,49 @@ __device__ __forceinline__ double lane_r2(double xk, int base, unsigned m3) {
   return __dadd_rn(__dadd_rn(s0, s1), s2);
 }
 
-// ---------------------------------------------------------------------------
+// Proposal of move m (Sec. 2, uniform displacement): lanes 0-2 of warp wb
+// form coordinate k of the trial position from Philox block (m, replica, 0),
+// lane 3 forms alpha from block (m, replica, 1).
+__device__ __forceinline__ void propose(const SysDev& S, MoveSetup& sh, unsigned long long m, unsigned replica,
+                                        uint2 key, double step, int wb) {
+  if ((int)(threadIdx.x >> 5) != wb || (threadIdx.x & 31) >= 4) return;
+  const int k = threadIdx.x & 31;
+  const uint4 u = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, k < 3 ? 0u : 1u), key);
+  if (k < 3) {
+    const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
+    const unsigned uk = k == 0 ? u.y : (k == 1 ? u.z : u.w);
+    const double src = (k == 0 ? S.px : (k == 1 ? S.py : S.pz))[i];
+    // (u 2^-32 + 2^-33) - 1/2 = (2u + 1 - 2^32) 2^-33 exactly (every step of the
+    // left side is exact in FP64), from one integer conversion
+    const double unit = __ll2double_rn(2LL * (long long)uk + 1LL - (1LL << 32)) * 0x1p-33;
+    sh.b[k] = __dadd_rn(src, __dmul_rn(unit, step));
+    if (k == 0) {
+      sh.i = i;
+      sh.dE = 0.0;
+      sh.flagged = 0;
+    }
+  } else {
+    sh.alpha = __ll2double_rn(2LL * (long long)u.x + 1LL) * 0x1p-33;  // (u + 1/2) 2^-32 exactly
+  }
+}
+
 // Set up the move of ion sh.i to sh.b (all threads; sh.i and sh.b written
 // before a barrier).  FP64 is slow on this part, so its work is spread over
 // lanes (x, y, z side by side) and warps: role 0 the ion and the trial point's
 // key and shell test, role 1 the trial image and its key, role 2 the image
 // charge.  Sets sh.outcome = -1 to proceed or the rejection outcome, with the
 // tests in the oracle's order: root cube, shell, image, image in root cube.
-static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+static __device__ void setup_roles(const SysDev& S, MoveSetup& sh, int wb) {
   TravPts& T = sh.T;
   const int i = sh.i;
   int k, base;
-  if (setup_role(0, k, base)) {
+  // The lanes of a role first load one 8-byte value each in a single
+  // instruction (divergent loads would wait for one another), then compute.
+  if (setup_role(0, wb, k, base)) {
     const unsigned m3 = 7u << base;
+    const unsigned long long* src =
+        reinterpret_cast<const unsigned long long*>(k < 3 ? (k == 0 ? S.px : (k == 1 ? S.py : S.pz)) : S.pq);
+    const unsigned long long val = k == 4 ? S.ckey[i] : src[i];  // a_k, q, key of the ion
     if (k < 3) {
       const double bk = sh.b[k];
       const unsigned long long kb = lane_key(S, bk, k, base, m3);
@@ -113,53 +150,52 @@ static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
         T.n_excl = sh.nmov;
         T.excl[0] = i;
       }
+      sh.a[k] = __longlong_as_double((long long)val);
     } else if (k == 3) {
-      sh.q = S.pq[i];
+      sh.q = __longlong_as_double((long long)val);
     } else if (k == 4) {
-      const unsigned long long ck = S.ckey[i];
-      T.pkey[0] = ck;
-      T.ekey[0] = ck;
-    } else {
-      sh.a[k - 5] = (k == 5 ? S.px : (k == 6 ? S.py : S.pz))[i];
+      T.pkey[0] = val;
+      T.ekey[0] = val;
     }
   }
-  if (setup_role(1, k, base)) {
+  if (setup_role(1, wb, k, base)) {
     const unsigned m3 = 7u << base;
     if (!S.images) {
       if (k == 0) {
         sh.rej_img = 0;
         sh.qa_img = 0.0;
       }
-    } else if (k < 3) {
-      const double bk = sh.b[k];
-      const double r2 = lane_r2(bk, base, m3);
-      double bik = 0.0;
-      unsigned long long kb = 0ULL;
-      if (r2 > 0.0) {
-        bik = __dmul_rn(__ddiv_rn(S.img_R2, r2), bk);
-        kb = lane_key(S, bik, k, base, m3);
-      }
-      sh.bi[k] = kb ? bik : 0.0;
-      if (k == 0) {
-        T.pkey[3] = kb;
-        sh.rej_img = kb == 0ULL;
-      }
     } else {
       const int img = S.n_mob + S.n_fix + i;
-      if (k == 3) {
-        sh.img = img;
-        T.excl[1] = img;
-        sh.qa_img = S.pq[img];
+      const unsigned long long* src =
+          reinterpret_cast<const unsigned long long*>(k < 3 ? (k == 0 ? S.px : (k == 1 ? S.py : S.pz)) : S.pq);
+      const unsigned long long val = k == 4 ? S.ckey[img] : src[img];  // a'_k, q', key of the image
+      if (k < 3) {
+        const double bk = sh.b[k];
+        const double r2 = lane_r2(bk, base, m3);
+        double bik = 0.0;
+        unsigned long long kb = 0ULL;
+        if (r2 > 0.0) {
+          bik = __dmul_rn(__ddiv_rn(S.img_R2, r2), bk);
+          kb = lane_key(S, bik, k, base, m3);
+        }
+        sh.bi[k] = kb ? bik : 0.0;
+        sh.ai[k] = __longlong_as_double((long long)val);
+        if (k == 0) {
+          T.pkey[3] = kb;
+          sh.rej_img = kb == 0ULL;
+          sh.img = img;
+          T.excl[1] = img;
+        }
+      } else if (k == 3) {
+        sh.qa_img = __longlong_as_double((long long)val);
       } else if (k == 4) {
-        const unsigned long long ck = S.ckey[img];
-        T.pkey[2] = ck;
-        T.ekey[1] = ck;
-      } else {
-        sh.ai[k - 5] = (k == 5 ? S.px : (k == 6 ? S.py : S.pz))[img];
+        T.pkey[2] = val;
+        T.ekey[1] = val;
       }
     }
   }
-  if (setup_role(2, k, base)) {
+  if (setup_role(2, wb, k, base)) {
     const unsigned m3 = 7u << base;
     if (!S.images) {
       if (k == 0) sh.qb_img = 0.0;
@@ -172,49 +208,70 @@ static __device__ void setup_move(const SysDev& S, MoveSh& sh) {
       }
     }
   }
-  __syncthreads();
-  if (warp == 0) {
-    if (lane == 0) {
-      sh.outcome = sh.rej_dom ? BHMC_REJECT_DOMAIN
-                              : sh.rej_shell ? BHMC_REJECT_OVERLAP : sh.rej_img ? BHMC_REJECT_DOMAIN : -1;
-      if (sh.rej_img) sh.qb_img = 0.0;
-    }
-    if (lane < 3 * sh.npts) {
-      const int s = lane / 3, k = lane - 3 * (lane / 3);
-      const double* pts[4] = {sh.a, sh.b, sh.ai, sh.bi};
-      const float2 f = split2(pts[s][k]);
-      T.x[s][k] = pts[s][k];
-      T.hi[s][k] = f.x;
-      T.lo[s][k] = f.y;
-      reinterpret_cast<float*>(&T.h4[s])[k] = f.x;
-      reinterpret_cast<float*>(&T.l4[s])[k] = f.y;
+}
+
+// Outcome of the rejection tests, float pairs of the points and weights (warp
+// wb).  Every lane converts one value in the same instruction stream: lane l <
+// 12 coordinate l % 3 of point l / 3, 12-15 the weight of point l - 12, 16-17
+// the charge of excluded charge l - 16.
+static __device__ void setup_finish(const SysDev& S, MoveSetup& sh, int wb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp != wb) return;
+  TravPts& T = sh.T;
+  const int np = sh.npts;
+  const int s = lane / 3, k = lane - 3 * (lane / 3);
+  double v = 0.0;
+  if (lane < 12) {
+    const double* pts[4] = {sh.a, sh.b, sh.ai, sh.bi};
+    if (s < np) v = pts[s][k];
+  } else if (lane < 16) {
+    const int t = lane - 12;
+    v = t == 0 ? -sh.q : (t == 1 ? sh.q : (t == 2 ? -sh.qa_img : (sh.rej_img ? 0.0 : sh.qb_img)));
+  } else if (lane < 18) {
+    v = lane == 16 ? sh.q : sh.qa_img;
+  }
+  const float hi = __double2float_rn(v);
+  const float lo = __double2float_rn(__dsub_rn(v, (double)hi));
+  if (lane < 12) {
+    if (s < np) {
+      T.x[s][k] = v;
+      T.hi[s][k] = hi;
+      T.lo[s][k] = lo;
+      reinterpret_cast<float*>(&T.h4[s])[k] = hi;
+      reinterpret_cast<float*>(&T.l4[s])[k] = lo;
       if (s == 0 || s == 2) {
-        T.ex[s >> 1][k] = pts[s][k];
-        T.ehi[s >> 1][k] = f.x;
-        T.elo[s >> 1][k] = f.y;
+        T.ex[s >> 1][k] = v;
+        T.ehi[s >> 1][k] = hi;
+        T.elo[s >> 1][k] = lo;
       }
-    } else if (lane >= 12 && lane < 12 + 3 * (4 - sh.npts)) {
+    } else {
       // unused points sit far outside the root so that they never touch a cluster
-      const int s = sh.npts + (lane - 12) / 3, k = (lane - 12) % 3;
       reinterpret_cast<float*>(&T.h4[s])[k] = 3.0e38f;
       reinterpret_cast<float*>(&T.l4[s])[k] = 0.0f;
-      T.pkey[s] = 0ULL;
+      if (k == 0) T.pkey[s] = 0ULL;
     }
-    if (lane == 31) {
-      const double w[4] = {-sh.q, sh.q, -sh.qa_img, sh.qb_img};
-      for (int s = 0; s < sh.npts; ++s) {
-        T.w64[s] = w[s];
-        T.w[s] = (float)w[s];
-      }
-      T.eq[0] = sh.q;
-      T.eqf[0] = (float)sh.q;
-      if (sh.nmov > 1) {
-        T.eq[1] = sh.qa_img;
-        T.eqf[1] = (float)sh.qa_img;
-      }
+  } else if (lane < 16) {
+    const int t = lane - 12;
+    if (t < np) {
+      T.w64[t] = v;
+      T.w[t] = hi;
     }
+  } else if (lane < 18) {
+    const int t = lane - 16;
+    if (t < sh.nmov) {
+      T.eq[t] = v;
+      T.eqf[t] = hi;
+    }
+  } else if (lane == 31) {
+    sh.outcome = sh.rej_dom ? BHMC_REJECT_DOMAIN
+                            : sh.rej_shell ? BHMC_REJECT_OVERLAP : sh.rej_img ? BHMC_REJECT_DOMAIN : -1;
   }
-  (void)W;
+}
+
+static __device__ void setup_move(const SysDev& S, MoveSetup& sh) {
+  setup_roles(S, sh, 0);
+  __syncthreads();
+  setup_finish(S, sh, 0);
 }
 
 // All warps: traverse, then thread 0 assembles dE (FP64).  Requires a
@@ -453,55 +510,57 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
   if (tid == 1 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
   if (tid < 2) sh.merge_d[tid] = 1 << 20;
   __syncthreads();
-  // (A1) FP64 moments per level: same cluster -> M += mb - ma, else M_old -= ma
-  // and M_new += mb; ion first, image second (their paths share clusters).
-  // With the image's pass thread 0 moves the leaf slots and the other threads
-  // update the counts along the paths.
-  for (int m = 0; m < sh.nmov; ++m) {
-    const int pa = 2 * m, pb = 2 * m + 1;
-    const int La = sh.plen[pa], Lb = sh.plen[pb];
-    const int Dn = max(La, Lb) + 1;
-    const double qa = m ? sh.qa_img : sh.q, qb = m ? sh.qb_img : sh.q;
-    for (int it = tid; it < Dn * K; it += nth) {
+  // (A1) FP64 moments per level, both moved charges in one pass: for each
+  // (level, term) the ion's update, then the image's (their paths share
+  // clusters, and a cluster belongs to one level, so one thread owns each
+  // (cluster, term)); same cluster -> M += mb - ma, else M_old -= ma and
+  // M_new += mb.  The last thread moves the leaf slots meanwhile.
+  {
+    int Dn = 0;
+    for (int ps = 0; ps < 2 * sh.nmov; ++ps) Dn = max(Dn, sh.plen[ps] + 1);
+    const int nw = nth - 1;
+    if (tid == nw) move_slots(S, sh);
+    for (int it = tid; tid < nw && it < Dn * K; it += nw) {
       const int d = it / K, t = it - d * K;
-      const int na = d <= La ? sh.path[pa][d] : -1;
-      const int nb = d <= Lb ? sh.path[pb][d] : -1;
       const int n1 = sh.ex[t][0], n2 = sh.ex[t][1], n3 = sh.ex[t][2];
-      double ma = 0.0, mb = 0.0;
-      if (na >= 0)
-        ma = __dmul_rn(qa, __dmul_rn(__dmul_rn(st.pw[m][0][d][0][n1], st.pw[m][0][d][1][n2]),
-                                     st.pw[m][0][d][2][n3]));
-      if (nb >= 0)
-        mb = __dmul_rn(qb, __dmul_rn(__dmul_rn(st.pw[m][1][d][0][n1], st.pw[m][1][d][1][n2]),
-                                     st.pw[m][1][d][2][n3]));
-      if (na >= 0 && na == nb) {
-        double* M = &S.M64[(size_t)na * K + t];
-        *M = __dadd_rn(*M, __dsub_rn(mb, ma));
-        mirror(S, na, t, *M);
-      } else {
-        if (na >= 0) {
+      for (int m = 0; m < sh.nmov; ++m) {
+        const int pa = 2 * m, pb = 2 * m + 1;
+        const int na = d <= sh.plen[pa] ? sh.path[pa][d] : -1;
+        const int nb = d <= sh.plen[pb] ? sh.path[pb][d] : -1;
+        const double qa = m ? sh.qa_img : sh.q, qb = m ? sh.qb_img : sh.q;
+        double ma = 0.0, mb = 0.0;
+        if (na >= 0)
+          ma = __dmul_rn(qa, __dmul_rn(__dmul_rn(st.pw[m][0][d][0][n1], st.pw[m][0][d][1][n2]),
+                                       st.pw[m][0][d][2][n3]));
+        if (nb >= 0)
+          mb = __dmul_rn(qb, __dmul_rn(__dmul_rn(st.pw[m][1][d][0][n1], st.pw[m][1][d][1][n2]),
+                                       st.pw[m][1][d][2][n3]));
+        if (na >= 0 && na == nb) {
           double* M = &S.M64[(size_t)na * K + t];
-          *M = __dsub_rn(*M, ma);
+          *M = __dadd_rn(*M, __dsub_rn(mb, ma));
           mirror(S, na, t, *M);
-        }
-        if (nb >= 0) {
-          double* M = &S.M64[(size_t)nb * K + t];
-          *M = __dadd_rn(*M, mb);
-          mirror(S, nb, t, *M);
+        } else {
+          if (na >= 0) {
+            double* M = &S.M64[(size_t)na * K + t];
+            *M = __dsub_rn(*M, ma);
+            mirror(S, na, t, *M);
+          }
+          if (nb >= 0) {
+            double* M = &S.M64[(size_t)nb * K + t];
+            *M = __dadd_rn(*M, mb);
+            mirror(S, nb, t, *M);
+          }
         }
       }
     }
-    if (m == sh.nmov - 1) {
-      if (tid == 0) move_slots(S, sh);
-      for (int it = tid; it < sh.nmov * NL; it += nth) {
-        const int mm = it / NL, d = it - mm * NL;
-        const int pa2 = 2 * mm, pb2 = 2 * mm + 1;
-        const int na = d <= sh.plen[pa2] ? sh.path[pa2][d] : -1;
-        const int nb = d <= sh.plen[pb2] ? sh.path[pb2][d] : -1;
-        if (na != nb) {
-          if (na >= 0) atomicSub(count_ptr(S, na), 1);
-          if (nb >= 0) atomicAdd(count_ptr(S, nb), 1);
-        }
+    for (int it = tid; it < sh.nmov * NL; it += nth) {
+      const int mm = it / NL, d = it - mm * NL;
+      const int pa2 = 2 * mm, pb2 = 2 * mm + 1;
+      const int na = d <= sh.plen[pa2] ? sh.path[pa2][d] : -1;
+      const int nb = d <= sh.plen[pb2] ? sh.path[pb2][d] : -1;
+      if (na != nb) {
+        if (na >= 0) atomicSub(count_ptr(S, na), 1);
+        if (nb >= 0) atomicAdd(count_ptr(S, nb), 1);
       }
     }
     __syncthreads();
@@ -631,43 +690,50 @@ struct MoveRec {
   int outcome, flagged;
 };
 
+// Barrier of warps 1-3 (the lookahead setup of the next move).
+__device__ __forceinline__ void bar_ahead() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+
 // One full trial move m of a chain (all threads).  Returns the outcome, or -1
-// after a device error (recorded in S.err).
+// after a device error (recorded in S.err).  With `ahead` (blocks of at least
+// four warps), warps 1-3 set up move m + 1 into sh.nxt while move m is
+// decided; move m + 1 uses it unless move m moved the same ion (the setup
+// reads nothing else that a move changes), so the chain is unchanged.
 template <int P, typename Real, int LAYOUT>
 __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica,
-                       uint2 key, double step, MoveRec* rec) {
+                       uint2 key, double step, MoveRec* rec, bool ahead) {
   MoveSh& sh = st.sh;
-  if (threadIdx.x < 4) {
-    // lanes 0-2: coordinate k of the trial position from block (m, replica, 0);
-    // lane 3: alpha from block (m, replica, 1)
-    const int k = threadIdx.x;
-    const uint4 u = philox(make_uint4((unsigned)m, (unsigned)(m >> 32), replica, k < 3 ? 0u : 1u), key);
-    if (k < 3) {
-      const int i = (int)(((unsigned long long)u.x * (unsigned long long)S.n_mob) >> 32);
-      const unsigned uk = k == 0 ? u.y : (k == 1 ? u.z : u.w);
-      const double src = (k == 0 ? S.px : (k == 1 ? S.py : S.pz))[i];
-      const double delta =
-          __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)uk, 0x1p-32), 0x1p-33), 0.5), step);
-      sh.b[k] = __dadd_rn(src, delta);
-      if (k == 0) {
-        sh.i = i;
-        sh.dE = 0.0;
-        sh.flagged = 0;
-      }
-    } else {
-      sh.alpha = __dmul_rn(__dadd_rn((double)u.x, 0.5), 0x1p-32);
-    }
+  const int warp = threadIdx.x >> 5;
+  ahead = ahead && blockDim.x >= 128;
+  if (sh.nxt_m == m) {
+    constexpr int n = (int)(sizeof(MoveSetup) / sizeof(int));
+    int* dst = reinterpret_cast<int*>(static_cast<MoveSetup*>(&sh));
+    const int* src = reinterpret_cast<const int*>(&sh.nxt);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+  } else {
+    propose(S, sh, m, replica, key, step, 0);
+    __syncthreads();
+    setup_roles(S, sh, 0);
+    __syncthreads();
+    setup_finish(S, sh, 0);
   }
   __syncthreads();
-  setup_move(S, sh);
-  __syncthreads();
+  if (threadIdx.x == 0) sh.nxt_m = ~0ULL;
   if (sh.outcome < 0) {
     eval_move<P, Real, LAYOUT>(S, st, true);
     if (sh.cnt[0][4]) {
       if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
       return -1;
     }
-    complete_paths(S, sh);
+    if (ahead && warp >= 1 && warp <= 3) {
+      propose(S, sh.nxt, m + 1, replica, key, step, 1);
+      bar_ahead();
+      setup_roles(S, sh.nxt, 1);
+      bar_ahead();
+      setup_finish(S, sh.nxt, 1);
+      if (threadIdx.x == 32) sh.nxt_m = m + 1;
+    } else {
+      complete_paths(S, sh);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       int acc, fl;
@@ -686,14 +752,17 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
       if (threadIdx.x == 0) *S.energy += sh.dE;
     }
   }
-  if (threadIdx.x == 0 && rec) {
-    rec->i = sh.i;
-    rec->r[0] = sh.b[0];
-    rec->r[1] = sh.b[1];
-    rec->r[2] = sh.b[2];
-    rec->dE = sh.dE;
-    rec->outcome = sh.outcome;
-    rec->flagged = sh.flagged;
+  if (threadIdx.x == 0) {
+    if (sh.outcome == BHMC_ACCEPT && sh.nxt.i == sh.i) sh.nxt_m = ~0ULL;
+    if (rec) {
+      rec->i = sh.i;
+      rec->r[0] = sh.b[0];
+      rec->r[1] = sh.b[1];
+      rec->r[2] = sh.b[2];
+      rec->dE = sh.dE;
+      rec->outcome = sh.outcome;
+      rec->flagged = sh.flagged;
+    }
   }
   __syncthreads();
   return sh.outcome;
@@ -894,7 +963,9 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step(SysDev S, unsigned
   __shared__ MoveStore st;
   if (*(volatile int*)S.err) return;
   init_tables(st.sh, S.K);
-  const int o = mc_move<P, Real, LAYOUT>(S, st, m, replica, key, step, recs);
+  if (threadIdx.x == 0) st.sh.nxt_m = ~0ULL;
+  __syncthreads();
+  const int o = mc_move<P, Real, LAYOUT>(S, st, m, replica, key, step, recs, false);
   if (threadIdx.x == 0 && o >= 0) {
     tally(stats, o, st.sh.flagged);
     stats->energy = *S.energy;
@@ -932,7 +1003,10 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
     __syncthreads();
     const int r = rep;
     if (r >= n_rep) break;
-    if (threadIdx.x == 0) S = views[r];
+    if (threadIdx.x == 0) {
+      S = views[r];
+      st.sh.nxt_m = ~0ULL;
+    }
     __syncthreads();
     const unsigned long long seed = args->seeds[r];
     const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
@@ -942,7 +1016,7 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
     for (unsigned long long t = 0; t < args->n_moves; ++t) {
       if (*(volatile int*)S.err) break;
       const int o = mc_move<P, Real, LAYOUT>(S, st, args->move0 + t, (unsigned)r, key, args->step,
-                                             nullptr);
+                                             nullptr, t + 1 < args->n_moves);
       if (o < 0) break;
       if (threadIdx.x == 0) tally(&loc, o, st.sh.flagged);
     }

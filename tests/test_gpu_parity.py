@@ -183,10 +183,13 @@ def test_mc_chain_colloid(bh, oracle_mod):
     assert ctx.export_tree() == ref.export_tree()
 
 
-def test_batch_replicas_match_oracle_chains(bh, oracle_mod):
+@pytest.mark.parametrize("warps", [2, 8])
+def test_batch_replicas_match_oracle_chains(bh, oracle_mod, warps):
+    """Persistent batched chains against the oracle's; with 8 warps the next
+    move's setup is computed while the current move is decided."""
     sizes = [660, 1000, 760, 900]
     systems = W.batch(sizes=sizes)
-    batch = bh.Batch(systems, warps=2)
+    batch = bh.Batch(systems, warps=warps)
     seeds = [1000 + r for r in range(len(sizes))]
     stats = batch.step_mc(150, 1.0, seeds)
     stats2 = batch.step_mc(100, 1.0, seeds, move0=150)
