@@ -22,11 +22,6 @@ struct MoveRec {
   double dE;
   int outcome, flagged;
 };
-struct BatchArgs {
-  unsigned long long n_moves, move0;
-  double step;
-  const unsigned long long* seeds;
-};
 }  // namespace bhmc
 
 using namespace bhmc;
@@ -51,6 +46,7 @@ struct bhmc_batch {
   BatchArgs* d_args = nullptr;
   BatchArgs* h_args = nullptr;
   unsigned long long* d_seeds = nullptr;
+  int* d_order = nullptr;
   int* d_next = nullptr;
   bhmc_mc_stats* d_stats = nullptr;
   bhmc_mc_stats* h_stats = nullptr;
@@ -697,8 +693,9 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   }
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
-  // the FP32 pass evaluates from W32, refreshed here from the running moments
-  bool ok = (ctx->S.prec != BHMC_PREC_F32 || !ctx->w_stale || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
+  // the FP32 pass at p = 6 evaluates from W32, refreshed here after moves
+  const bool wform = ctx->S.prec == BHMC_PREC_F32 && ctx->S.p >= 6;
+  bool ok = (!wform || !ctx->w_stale || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
             cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
             dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
@@ -895,10 +892,21 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
       cudaMallocHost(&B->h_args, sizeof(BatchArgs)) != cudaSuccess ||
       cudaMalloc(&B->d_seeds, sizeof(unsigned long long) * n_rep) != cudaSuccess ||
       cudaMalloc(&B->d_next, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&B->d_order, sizeof(int) * n_rep) != cudaSuccess ||
       cudaMalloc(&B->d_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess ||
       cudaMallocHost(&B->h_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess) {
     bhmc_batch_destroy(B);
     return BHMC_ENOMEM;
+  }
+  // Blocks take replicas largest first: the first block on each SM gets one of
+  // the largest systems, the second blocks (on some SMs) the smallest, which
+  // finish early and leave their SM to the large chain.
+  std::vector<int> order(n_rep);
+  for (int r = 0; r < n_rep; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return views[x].n_tot > views[y].n_tot; });
+  if (cudaMemcpy(B->d_order, order.data(), sizeof(int) * n_rep, cudaMemcpyHostToDevice) != cudaSuccess) {
+    bhmc_batch_destroy(B);
+    return BHMC_ECUDA;
   }
   if (cudaMemcpy(B->d_views, views.data(), sizeof(SysDev) * n_rep, cudaMemcpyHostToDevice) != cudaSuccess) {
     bhmc_batch_destroy(B);
@@ -957,6 +965,7 @@ bhmc_status bhmc_batch_destroy(bhmc_batch* B) {
   cudaFreeHost(B->h_args);
   cudaFree(B->d_seeds);
   cudaFree(B->d_next);
+  cudaFree(B->d_order);
   cudaFree(B->d_stats);
   cudaFreeHost(B->h_stats);
   delete B;
@@ -985,6 +994,7 @@ bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, con
   B->h_args->move0 = move0;
   B->h_args->step = step;
   B->h_args->seeds = B->d_seeds;
+  B->h_args->order = B->d_order;
   CK(cudaGraphLaunch(B->graph, B->stream));
   bhmc_status rc = BHMC_OK;
   for (bhmc_ctx* c : B->reps) {

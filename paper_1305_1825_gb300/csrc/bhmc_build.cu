@@ -203,8 +203,10 @@ __global__ void k_moments_leaves(SysDev S, int n_nodes, const int* perm, const i
 }
 
 // Internal clusters of one level from their eight children (moments shifted
-// from the child centre to the parent centre, both exact dyadic points):
+// from the child centre to the parent centre):
 // M_P^n = sum_children sum_{m <= n} C(n, m) d^(n - m) M_child^m, d = r_child - r_P.
+// Every component of d is +-h_c (the child's half side, a power of two), so each
+// coefficient C(n1,m1) C(n2,m2) C(n3,m3) h_c^(|n| - |m|) with its sign is exact.
 __global__ void k_moments_m2m(SysDev S, int node_begin, int node_end) {
   const long long total = (long long)(node_end - node_begin) * S.K;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
@@ -212,32 +214,26 @@ __global__ void k_moments_m2m(SysDev S, int node_begin, int node_end) {
     const int nd = node_begin + (int)(it / S.K), t = (int)(it % S.K);
     const int4 b = S.nB[nd];
     if ((b.z == 0 && b.w == 0) || b.x < 0) continue;
-    const float4 c = S.nA[nd];
     int n1, n2, n3;
     term_exponents(t, n1, n2, n3);
+    double hp[BHMC_MAX_P + 1];  // h_c^k
+    hp[0] = 1.0;
+    const double hc = (double)S.nA[b.x].w;
+    for (int q = 1; q <= n1 + n2 + n3; ++q) hp[q] = hp[q - 1] * hc;
     double M = 0.0;
     for (int o = 0; o < 8; ++o) {
-      const int ch = b.x + o;
-      const float4 cc = S.nA[ch];
-      const double d[3] = {(double)cc.x - (double)c.x, (double)cc.y - (double)c.y, (double)cc.z - (double)c.z};
-      const double* Mc = S.M64 + (size_t)ch * S.K;
-      double b1 = 1.0;  // C(n1, m1) d1^(n1 - m1), m1 from n1 down to 0
-      double p1 = 1.0;
-      for (int m1 = n1; m1 >= 0; --m1) {
-        double p2 = 1.0, b2 = 1.0;
-        for (int m2 = n2; m2 >= 0; --m2) {
-          double p3 = 1.0, b3 = 1.0;
+      const double* Mc = S.M64 + (size_t)(b.x + o) * S.K;
+      for (int m1 = n1; m1 >= 0; --m1)
+        for (int m2 = n2; m2 >= 0; --m2)
           for (int m3 = n3; m3 >= 0; --m3) {
-            M += (b1 * p1) * (b2 * p2) * (b3 * p3) * Mc[tidx(m1, m2, m3)];
-            p3 *= d[2];
-            b3 = b3 * (double)m3 / (double)(n3 - m3 + 1);
+            const int a1 = n1 - m1, a2 = n2 - m2, a3 = n3 - m3;
+            // odd powers of a negative component flip the sign (child o lies
+            // on the low side of axis k when bit k of o is clear)
+            const bool neg = (((o & 1) == 0) && (a1 & 1)) != (((o & 2) == 0) && (a2 & 1)) !=
+                             (((o & 4) == 0) && (a3 & 1));
+            const double cf = (double)(binom(n1, m1) * binom(n2, m2) * binom(n3, m3)) * hp[a1 + a2 + a3];
+            M = fma(neg ? -cf : cf, Mc[tidx(m1, m2, m3)], M);
           }
-          p2 *= d[1];
-          b2 = b2 * (double)m2 / (double)(n2 - m2 + 1);
-        }
-        p1 *= d[0];
-        b1 = b1 * (double)m1 / (double)(n1 - m1 + 1);
-      }
     }
     S.M64[(size_t)nd * S.K + t] = M;
     if (S.prec == BHMC_PREC_F32) S.M32[m32_index(S, nd, t)] = __double2float_rn(M);

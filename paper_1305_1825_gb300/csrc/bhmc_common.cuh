@@ -73,6 +73,14 @@ struct SysDev {
   int* err;
 };
 
+// Arguments of one batched launch (device memory).
+struct BatchArgs {
+  unsigned long long n_moves, move0;
+  double step;
+  const unsigned long long* seeds;
+  const int* order;  // replicas in the order blocks take them (largest first)
+};
+
 // --------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
@@ -190,6 +198,13 @@ __device__ __forceinline__ bool shell_ok(const SysDev& S, const double x[3]) {
 }
 
 __device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S.err, 0, code); }
+
+// Binomial coefficient C(n, m), 0 <= m <= n <= 10.
+__device__ __forceinline__ int binom(int n, int m) {
+  int c = 1;
+  for (int k = 1; k <= m; ++k) c = c * (n - m + k) / k;
+  return c;
+}
 
 // Moment term t (graded order) of charge q at offset d, in FP64 with the
 // monomial built by repeated multiplication: q * ((dx^n1 * dy^n2) * dz^n3).

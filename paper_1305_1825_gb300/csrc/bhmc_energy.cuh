@@ -43,7 +43,36 @@ __device__ __forceinline__ Real lane_multipole(const SysDev& S, const float4& a,
                                                const float hi[3], const float lo[3], bool self, double q,
                                                const float qhi[3], const float qlo[3]) {
   constexpr int K = nterms(P);
+  if (sizeof(Real) == 4 && P < 6) {
+    // the recurrence (measured faster than the coefficient form up to p = 4)
+    const float rx = (a.x - hi[0]) - lo[0], ry = (a.y - hi[1]) - lo[1], rz = (a.z - hi[2]) - lo[2];
+    float Tc[K];
+    taylor<P, float>(rx, ry, rz, Tc);
+    float v = 0.f;
+    if (LAYOUT == BHMC_LAYOUT_AOS) {
+      constexpr int KP = pad4(K);
+      const float4* M4 = reinterpret_cast<const float4*>(S.M32 + (size_t)node * KP);
+#pragma unroll
+      for (int t4 = 0; t4 < KP / 4; ++t4) {
+        const float4 m = M4[t4];
+        const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * t4 + u < K) v = fmaf(Tc[4 * t4 + u], mm[u], v);
+      }
+    } else {
+      const float* M = S.M32 + node;
+#pragma unroll
+      for (int t = 0; t < K; ++t) v = fmaf(Tc[t], M[(size_t)t * S.node_cap], v);
+    }
+    if (self) {  // the target's own charge lies in the cluster: remove its expansion
+      const float dx = (qhi[0] - a.x) + qlo[0], dy = (qhi[1] - a.y) + qlo[1], dz = (qhi[2] - a.z) + qlo[2];
+      v -= (float)q * dot_monomials<P, float>(Tc, dx, dy, dz);
+    }
+    return (Real)v;
+  }
   if (sizeof(Real) == 4) {
+    // p = 6: evaluation coefficients (a third of the recurrence's instructions)
     const float rx = (a.x - hi[0]) - lo[0], ry = (a.y - hi[1]) - lo[1], rz = (a.z - hi[2]) - lo[2];
     // the target's own charge, if it lies in the cluster, is removed through its expansion
     const float qe[1] = {(float)q};

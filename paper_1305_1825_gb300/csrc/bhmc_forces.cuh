@@ -18,7 +18,8 @@
 
 namespace bhmc {
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
     }
     const double qi = S.pq[i];
     const unsigned long long ki = S.ckey[i];
-    double phi = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    // per-lane sums in the traversal precision (compensated in FP32)
+    Acc<Real> phi, g0, g1, g2;
     const unsigned lanes = __ballot_sync(FULL, valid);
     if (lane == 0) E.e[0] = make_int4(0, (int)lanes, 0, 0);
     int top = 1;
@@ -137,15 +139,16 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
                 d0 -= Real(n1 + 1) * Tc[tidx(n1 + 1, n2, n3)] * m;
                 d1 -= Real(n2 + 1) * Tc[tidx(n1, n2 + 1, n3)] * m;
                 d2 -= Real(n3 + 1) * Tc[tidx(n1, n2, n3 + 1)] * m;
-                // cluster adjoint: one atomic per term and warp
-                const double l = warp_sum(mul ? qi * (double)Tc[t] : 0.0);
-                if (lane == 0) atomicAdd(&lam[(size_t)node * K + t], l);
+                // cluster adjoint: the warp's contributions summed in the
+                // traversal precision, one FP64 atomic per term and warp
+                const Real l = warp_sum<Real>(mul ? (Real)qi * Tc[t] : Real(0));
+                if (lane == 0) atomicAdd(&lam[(size_t)node * K + t], (double)l);
               }
           if (mul) {
-            phi += (double)v;
-            g0 += (double)d0;
-            g1 += (double)d1;
-            g2 += (double)d2;
+            phi.add(v);
+            g0.add(d0);
+            g1.add(d1);
+            g2.add(d2);
           }
         }
         const unsigned mo = __ballot_sync(FULL, opn), mf = __ballot_sync(FULL, fdv);
@@ -163,40 +166,42 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
             const float4 sa = S.sA[node * SC + k];
             const float4 sb = S.sB[node * SC + k];
             const int j = __float_as_int(sb.w);
-            double cp = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
+            Real cp = 0, c0 = 0, c1 = 0, c2 = 0;
             if (dir && j != i) {
-              double ex, ey, ez;
+              Real ex, ey, ez, qj;
               if (sizeof(Real) == 4) {
-                ex = (double)((sa.x - hi[0]) + (sb.x - lo[0]));
-                ey = (double)((sa.y - hi[1]) + (sb.y - lo[1]));
-                ez = (double)((sa.z - hi[2]) + (sb.z - lo[2]));
+                ex = (Real)((sa.x - hi[0]) + (sb.x - lo[0]));
+                ey = (Real)((sa.y - hi[1]) + (sb.y - lo[1]));
+                ez = (Real)((sa.z - hi[2]) + (sb.z - lo[2]));
+                qj = (Real)sa.w;
               } else {
-                ex = S.px[j] - x[0];
-                ey = S.py[j] - x[1];
-                ez = S.pz[j] - x[2];
+                ex = (Real)(S.px[j] - x[0]);
+                ey = (Real)(S.py[j] - x[1]);
+                ez = (Real)(S.pz[j] - x[2]);
+                qj = (Real)S.pq[j];
               }
-              const double r2 = ex * ex + ey * ey + ez * ez;
-              const double rinv = sizeof(Real) == 4 ? (double)rsqrtf((float)r2) : 1.0 / sqrt(r2);
-              const double r3inv = rinv * rinv * rinv;
-              const double qj = sizeof(Real) == 4 ? (double)sa.w : S.pq[j];
-              phi += qj * rinv;
-              g0 += qj * ex * r3inv;
-              g1 += qj * ey * r3inv;
-              g2 += qj * ez * r3inv;
-              cp = qi * rinv;
-              c0 = -qi * qj * ex * r3inv;
-              c1 = -qi * qj * ey * r3inv;
-              c2 = -qi * qj * ez * r3inv;
+              const Real r2 = ex * ex + ey * ey + ez * ez;
+              const Real rinv = rsqrt_t<Real>(r2);
+              const Real r3inv = rinv * rinv * rinv;
+              phi.add(qj * rinv);
+              g0.add(qj * ex * r3inv);
+              g1.add(qj * ey * r3inv);
+              g2.add(qj * ez * r3inv);
+              const Real qr = (Real)qi;
+              cp = qr * rinv;
+              c0 = -qr * qj * ex * r3inv;
+              c1 = -qr * qj * ey * r3inv;
+              c2 = -qr * qj * ez * r3inv;
             }
-            cp = warp_sum(cp);
-            c0 = warp_sum(c0);
-            c1 = warp_sum(c1);
-            c2 = warp_sum(c2);
-            if (lane == 0 && (cp != 0.0 || c0 != 0.0 || c1 != 0.0 || c2 != 0.0)) {
-              atomicAdd(&psi[j], cp);
-              atomicAdd(&src[3 * j + 0], c0);
-              atomicAdd(&src[3 * j + 1], c1);
-              atomicAdd(&src[3 * j + 2], c2);
+            cp = warp_sum<Real>(cp);
+            c0 = warp_sum<Real>(c0);
+            c1 = warp_sum<Real>(c1);
+            c2 = warp_sum<Real>(c2);
+            if (lane == 0 && (cp != Real(0) || c0 != Real(0) || c1 != Real(0) || c2 != Real(0))) {
+              atomicAdd(&psi[j], (double)cp);
+              atomicAdd(&src[3 * j + 0], (double)c0);
+              atomicAdd(&src[3 * j + 1], (double)c1);
+              atomicAdd(&src[3 * j + 2], (double)c2);
             }
           }
         }
@@ -204,10 +209,10 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
       __syncwarp();
     }
     if (valid) {
-      phi_out[i] = phi;
-      tgrad[3 * i + 0] = qi * g0;
-      tgrad[3 * i + 1] = qi * g1;
-      tgrad[3 * i + 2] = qi * g2;
+      phi_out[i] = phi.value();
+      tgrad[3 * i + 0] = qi * g0.value();
+      tgrad[3 * i + 1] = qi * g1.value();
+      tgrad[3 * i + 2] = qi * g2.value();
     }
     __syncwarp();
   }

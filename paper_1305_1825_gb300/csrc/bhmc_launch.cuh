@@ -8,7 +8,6 @@ namespace bhmc {
 
 struct DeltaOut;
 struct MoveRec;
-struct BatchArgs;
 
 template <int P>
 cudaError_t launch_delta(const SysDev& S, int warps, int i, const double* b, DeltaOut* out,

@@ -985,11 +985,6 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step_mala(SysDev S, uns
   }
 }
 
-struct BatchArgs {
-  unsigned long long n_moves, move0;
-  double step;
-  const unsigned long long* seeds;
-};
 
 template <int P, typename Real, int LAYOUT>
 __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
@@ -999,7 +994,10 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
   __shared__ SysDev S;
   init_tables(st.sh, nterms(P));
   for (;;) {
-    if (threadIdx.x == 0) rep = atomicAdd(next, 1);
+    if (threadIdx.x == 0) {
+      const int q = atomicAdd(next, 1);
+      rep = q < n_rep ? args->order[q] : n_rep;
+    }
     __syncthreads();
     const int r = rep;
     if (r >= n_rep) break;

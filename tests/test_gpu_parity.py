@@ -233,3 +233,37 @@ def test_energy_counters_match_oracle(bh, oracle_mod, precision):
         e = ref.phi(x[j], excl=[j])
         want += (e.visited, e.accepted, e.pairs)
     assert (cnt.visited, cnt.accepted, cnt.pairs) == tuple(int(v) for v in want)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("p", [4, 6])
+def test_energy_after_chain(bh, oracle_mod, layout, p):
+    """The full-energy pass after a chain of accepted moves (at p = 6 it
+    evaluates coefficients refreshed from the running moments) against the
+    oracle's treecode energy of the same final configuration."""
+    wl = W.colloid(n=1200, seed=13, p=p)
+    ctx = bh.Context(wl, warps=8, layout=layout)
+    ref = _oracle(oracle_mod, wl)
+    st, rec = ctx.step_mc(400, 1.0, seed=5, records=True)
+    orec = ref.mc_run(5, 400)
+    assert _compare_chain(rec, orec) == 400
+    assert st.accepted > 200
+    e_tree = ctx.energy()
+    e_ref = ref.energy_tree()
+    scale = float(np.abs(wl["q"]).sum())
+    assert abs(e_tree - e_ref) <= 2e-6 * abs(e_ref) + 2e-6 * scale
+
+
+@pytest.mark.parametrize("p", [2, 6])
+def test_potentials_sampled(bh, oracle_mod, p):
+    """Per-charge treecode potentials of the full-energy pass (recurrence at
+    p = 2, evaluation coefficients at p = 6) against the oracle, sampled."""
+    wl = W.colloid(n=2000, seed=14, p=p)
+    ctx = bh.Context(wl, warps=4, layout=1)
+    ref = _oracle(oracle_mod, wl)
+    phi = ctx.potentials()
+    q, x = ref.charges()
+    rng = np.random.default_rng(p)
+    for j in rng.choice(len(q), 150, replace=False):
+        e = ref.phi(x[j], excl=[int(j)])
+        assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
