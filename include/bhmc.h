@@ -75,6 +75,10 @@ typedef struct {
   int32_t warps;      /* warps cooperating on one move: 1, 2, 4 or 8 */
   int32_t layout;     /* BHMC_LAYOUT_SOA or BHMC_LAYOUT_AOS for the FP32 moment mirror */
   double node_factor; /* node pool = 64 + node_factor * charges (0 selects 2.0) */
+  double hard_core;   /* common diameter tau of the mobile ions (Eq. 2.1: the pair potential is
+                         infinite for r_ij <= tau); a trial position within tau of another mobile
+                         ion is rejected (BHMC_REJECT_OVERLAP); 0 disables.  Images and fixed
+                         charges carry no hard core (the macroion's is the shell). */
 } bhmc_params;
 
 typedef struct bhmc_ctx bhmc_ctx;

@@ -43,6 +43,7 @@ class Params(C.Structure):
         ("root_lo", C.c_double * 3), ("root_side", C.c_double),
         ("shell", C.c_int32), ("shell_rmin", C.c_double), ("shell_rmax", C.c_double),
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
+        ("hard_core", C.c_double),
     ]
 
 
@@ -173,6 +174,7 @@ def make_params(d: dict) -> Params:
     P.shell_rmin, P.shell_rmax = (d["shell"] if d.get("shell") else (0.0, 0.0))
     P.images = 1 if d.get("image") else 0
     P.image_R, P.image_alpha = (d["image"] if d.get("image") else (0.0, 0.0))
+    P.hard_core = d.get("hard_core", 0.0) or 0.0
     return P
 
 

@@ -387,6 +387,18 @@ void or_destroy(or_sys* s) {
   free(s);
 }
 
+/* Hard core of Eq. (2.1) between mobile ions of common diameter tau: the pair
+   potential is infinite for r_ij <= tau, i.e. (dx dx + dy dy) + dz dz <= tau^2. */
+static int hard_core_overlap(const or_sys* s, int64_t i, const double b[3]) {
+  const double t2 = s->P.hard_core * s->P.hard_core;
+  for (int64_t j = 0; j < s->n_mob; ++j) {
+    if (j == i) continue;
+    const double dx = b[0] - s->x[3 * j], dy = b[1] - s->x[3 * j + 1], dz = b[2] - s->x[3 * j + 2];
+    if ((dx * dx + dy * dy) + dz * dz <= t2) return 1;
+  }
+  return 0;
+}
+
 or_sys* or_create(const or_params* P, int64_t n_mob, int64_t n_fix, const double* q,
                   const double* xyz, int* status) {
   *status = OR_EINVAL;
@@ -433,6 +445,15 @@ or_sys* or_create(const or_params* P, int64_t n_mob, int64_t n_fix, const double
       *status = OR_EOVERLAP;
       or_destroy(s);
       return NULL;
+    }
+  }
+  if (P->hard_core > 0.0) {
+    for (int64_t i = 0; i < n_mob; ++i) {
+      if (hard_core_overlap(s, i, &s->x[3 * i])) {
+        *status = OR_EOVERLAP;
+        or_destroy(s);
+        return NULL;
+      }
     }
   }
   for (int64_t j = 0; j < s->n_tot; ++j) s->key[j] = or_point_key(s, &s->x[3 * j]);
@@ -623,6 +644,7 @@ static int prepare_move(const or_sys* s, int64_t i, const double b[3], or_move* 
     m->excl[1] = k;
     m->n_excl = 2;
   }
+  if (s->P.hard_core > 0.0 && hard_core_overlap(s, i, b)) return OR_EOVERLAP;
   return OR_OK;
 }
 

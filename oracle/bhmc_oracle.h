@@ -56,6 +56,7 @@ typedef struct {
   int32_t images;   /* 1: every mobile ion carries a point image that moves with it */
   double image_R;   /* image position R^2 r / |r|^2 */
   double image_alpha; /* image charge alpha * q * R / |r| */
+  double hard_core; /* common diameter tau of the mobile ions (Eq. 2.1), 0: none */
 } or_params;
 
 typedef struct or_sys or_sys;

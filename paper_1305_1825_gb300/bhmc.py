@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("shell", C.c_int32), ("shell_rmin", C.c_double), ("shell_rmax", C.c_double),
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
         ("precision", C.c_int32), ("warps", C.c_int32), ("layout", C.c_int32),
-        ("node_factor", C.c_double),
+        ("node_factor", C.c_double), ("hard_core", C.c_double),
     ]
 
 
@@ -148,6 +148,7 @@ def make_params(d: dict, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_fa
     P.warps = d.get("warps", warps)
     P.layout = d.get("layout", layout)
     P.node_factor = d.get("node_factor", node_factor)
+    P.hard_core = d.get("hard_core", 0.0) or 0.0
     return P
 
 

@@ -113,6 +113,7 @@ static bhmc_status validate(const bhmc_params* P) {
       P->warps > BHMC_MAX_WARPS)
     return BHMC_EINVAL;
   if (P->node_factor < 0.0) return BHMC_EINVAL;
+  if (!(P->hard_core >= 0.0) || !std::isfinite(P->hard_core)) return BHMC_EINVAL;
   return BHMC_OK;
 }
 
@@ -270,6 +271,8 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.rmin2 = S.rmin * S.rmin;
   S.rmax2 = S.rmax * S.rmax;
   S.img_R2 = S.img_R * S.img_R;
+  S.hc2 = P->hard_core * P->hard_core;
+  S.hc2f = (float)S.hc2;
   S.img_alpha = P->image_alpha;
   const double f = P->node_factor > 0.0 ? P->node_factor : (1.0 + std::max(1.0, 8.0 / P->C));
   long long cap = 64 + (long long)std::ceil(f * (double)S.n_tot);
@@ -398,12 +401,14 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
   if (cudaMemcpyAsync(S.pool, &groups, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(S.order, perm, sizeof(int) * S.n_tot, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       build_leaves_moments(S, 8 * groups, perm, seg, dflags, level_begin.data(), (int)level_begin.size(), st) != cudaSuccess ||
+      launch_hard_core_check(S, dflags, st) != cudaSuccess ||
       cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cleanup();
     return BHMC_ECUDA;
   }
   if (hflags[2]) rc = BHMC_ECAPACITY;
+  else if (hflags[1]) rc = BHMC_EOVERLAP;  // hard-core overlap in the initial configuration
   cleanup();
   return rc;
 }

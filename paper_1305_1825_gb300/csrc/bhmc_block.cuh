@@ -49,7 +49,7 @@ struct BlockStore {
   uint2 di[32 * BHMC_MAX_WARPS];         // {leaf, count << 4 | point mask}
   int wcnt[BHMC_MAX_WARPS][3];
   double wsum[BHMC_MAX_WARPS];
-  int wred[BHMC_MAX_WARPS][5];
+  int wred[BHMC_MAX_WARPS][6];
   double wg[BHMC_MAX_WARPS][8];
 };
 
@@ -68,6 +68,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   Acc<Real> acc;
   GradAcc<Real> ga;
   int visited = 0, accepted = 0, pairs = 0, fp64 = 0, err = 0;
+  const bool hc = S.hc2 > 0.0;  // hard cores (Eq. 2.1) at the trial point
+  bool ovl = false;
   int cp = 1;
   while (cp < S.C) cp <<= 1;
   const int lg = 31 - __clz(cp);
@@ -75,7 +77,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   int top = 0, npop = 1;
   // A stack entry is a group of eight sibling clusters: {first node, bits 0-3
   // points still traversing, bits 4-7 points summing directly, bits 8-11
-  // points whose own cluster is the group's parent, bits 12-16 depth}.
+  // points whose own cluster is the group's parent, bits 12-16 depth, bit 17
+  // reached only for the hard-core test of the trial point}.
   unsigned pm0 = 0;
 #pragma unroll
   for (int s = 0; s < 4; ++s) pm0 |= T.pkey[s] != 0ULL ? (1u << s) : 0u;
@@ -108,7 +111,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     bool have0 = false;
     if ((tid >> lg) < td_) {
       di0 = B.di[tid >> lg];
-      if (kk < (int)(di0.y >> 4)) {
+      if (kk < (int)((di0.y >> 4) & 0xffffu)) {
         const int slot = (int)di0.x * SC + kk;
         sa0 = S.sA[slot];
         sb0 = S.sB[slot];
@@ -132,17 +135,20 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         direct_slot_grad<Real>(S, T, sa0, sb0, di0.y & 15u, ga, pairs);
       else
         direct_slot<Real>(S, T, sa0, sb0, di0.y & 15u, acc, pairs);
+      if (hc && ((di0.y & 2u) || (di0.y >> 30))) ovl |= hc_slot(S, T, sa0, sb0);
     }
     for (int base = per; base < td_; base += per) {
       const int item = base + (tid >> lg);
       if (item < td_) {
         const uint2 di = B.di[item];
-        if (kk < (int)(di.y >> 4)) {
+        if (kk < (int)((di.y >> 4) & 0xffffu)) {
           const int slot = (int)di.x * SC + kk;
+          const float4 sa = S.sA[slot], sb = S.sB[slot];
           if (GRAD)
-            direct_slot_grad<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, ga, pairs);
+            direct_slot_grad<Real>(S, T, sa, sb, di.y & 15u, ga, pairs);
           else
-            direct_slot<Real>(S, T, S.sA[slot], S.sB[slot], di.y & 15u, acc, pairs);
+            direct_slot<Real>(S, T, sa, sb, di.y & 15u, acc, pairs);
+          if (hc && ((di.y & 2u) || (di.y >> 30))) ovl |= hc_slot(S, T, sa, sb);
         }
       }
     }
@@ -155,11 +161,13 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     }
     const int node = (int)e.x + (tid & 7);
     const unsigned om = e.y & 15u, fd = (e.y >> 4) & 15u, pmp = (e.y >> 8) & 15u;
-    const int d = (int)(e.y >> 12);
+    const int d = (int)((e.y >> 12) & 31u);
+    const bool ovin = ((e.y >> 17) & 1u) != 0u;
+    bool ovp = false, ovd = false;  // hard-core descent / leaf test for the trial point
     unsigned mac = 0, open = 0, fdc = 0, dir = 0, emask = 0, onp = 0;
     int fc = -1, cnt = 0;
     const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-    if (g < npop && (om | fd) && key != 0ULL) {
+    if (g < npop && ((om | fd) || ovin) && key != 0ULL) {
       fc = b.x;
       cnt = b.y;
       // points inside this cluster: those inside the parent whose octant at
@@ -229,16 +237,24 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         } else {
           dir = rest | fd;
         }
+        // hard core: a cluster the trial point accepted (or reached for this
+        // test only) may still hold ions within the diameter of it
+        if (hc && (ovin || (mac & 2u)) && hc_box(S, T, a)) {
+          if (fc >= 0)
+            ovp = true;
+          else
+            ovd = true;
+        }
         if (LAYOUT == BHMC_LAYOUT_AOS && mac)
           prefetch_range(S.M32 + (size_t)node * pad4(nterms(P)), pad4(nterms(P)) * 4);
-        if (dir) {
+        if (dir || ovd) {
           prefetch_range(S.sA + (size_t)node * SC, cnt * 16);
           prefetch_range(S.sB + (size_t)node * SC, cnt * 16);
         }
       }
     }
     // block-wide compaction of pushes, multipole items and direct items
-    const bool push = (open | fdc) != 0;
+    const bool push = (open | fdc) != 0 || ovp;
     const unsigned pb = __ballot_sync(FULL, push);
     const int nm = __popc(mac);
     int incl = nm;
@@ -247,7 +263,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       const int v = __shfl_up_sync(FULL, incl, o);
       if (lane >= o) incl += v;
     }
-    const unsigned db = __ballot_sync(FULL, dir != 0);
+    const unsigned db = __ballot_sync(FULL, dir != 0 || ovd);
     if (lane == 31) {
       B.wcnt[warp][0] = __popc(pb);
       B.wcnt[warp][1] = incl;
@@ -272,7 +288,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     }
     if (push)
       B.stk[top + op + __popc(pb & lt)] =
-          make_uint2((unsigned)fc, open | (fdc << 4) | (onp << 8) | ((unsigned)(d + 1) << 12));
+          make_uint2((unsigned)fc, open | (fdc << 4) | (onp << 8) | ((unsigned)(d + 1) << 12) |
+                                       (ovp ? (1u << 17) : 0u));
     {
       int pos = oi + incl - nm;
       unsigned m = mac;
@@ -282,7 +299,8 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         B.mi[pos++] = ((unsigned)node << 4) | (emask << 2) | (unsigned)s;
       }
     }
-    if (dir) B.di[od + __popc(db & lt)] = make_uint2((unsigned)node, ((unsigned)cnt << 4) | dir);
+    if (dir || ovd)
+      B.di[od + __popc(db & lt)] = make_uint2((unsigned)node, ((unsigned)cnt << 4) | dir | (ovd ? (1u << 30) : 0u));
     accepted += nm;
     top += tp;
     __syncthreads();
@@ -328,6 +346,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   const int r0 = __reduce_add_sync(FULL, visited), r1 = __reduce_add_sync(FULL, accepted);
   const int r2 = __reduce_add_sync(FULL, pairs), r3 = __reduce_add_sync(FULL, fp64);
   const int r4 = __reduce_max_sync(FULL, err);
+  const int r5 = __any_sync(FULL, ovl) ? 1 : 0;
   if (lane == 0) {
     B.wsum[warp] = v;
     if (GRAD) {
@@ -339,6 +358,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     B.wred[warp][2] = r2;
     B.wred[warp][3] = r3;
     B.wred[warp][4] = r4;
+    B.wred[warp][5] = r5;
   }
   __syncthreads();
   if (tid == 0) {
@@ -347,7 +367,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       out.phi[r] = 0.0;
       out.grad[r][0] = out.grad[r][1] = out.grad[r][2] = 0.0;
     }
-    out.visited = out.accepted = out.pairs = out.fp64 = out.err = 0;
+    out.visited = out.accepted = out.pairs = out.fp64 = out.err = out.overlap = 0;
     for (int w = 0; w < NW; ++w) {
       out.sum += B.wsum[w];
       if (GRAD)
@@ -359,6 +379,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       out.accepted += B.wred[w][1];
       out.pairs += B.wred[w][2];
       out.fp64 += B.wred[w][3];
+      out.overlap |= B.wred[w][5];
       out.err = max(out.err, B.wred[w][4]);
     }
   }

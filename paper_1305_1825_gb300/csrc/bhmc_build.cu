@@ -240,6 +240,59 @@ __global__ void k_moments_m2m(SysDev S, int node_begin, int node_end) {
   }
 }
 
+// Hard core of Eq. (2.1) in the initial configuration: flags[1] is set if two
+// mobile ions are within the diameter.  One thread per mobile ion walks the
+// clusters whose boxes come within the diameter of it (explicit stack of
+// 8-sibling groups, bounded) and tests their leaves' mobile charges in FP64.
+__global__ void k_hard_core_check(SysDev S, int* flags) {
+  constexpr int kStack = 8 * (BHMC_MAX_D + 2);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_mob; j += gridDim.x * blockDim.x) {
+    const double x[3] = {S.px[j], S.py[j], S.pz[j]};
+    int stack[kStack];
+    int top = 0;
+    const int4 root = S.nB[0];
+    bool hit = false;
+    if (root.x < 0) {  // the root is a leaf
+      for (int k = 0; k < root.y && !hit; ++k) {
+        const int m = __float_as_int(S.sB[k].w);
+        if (m >= S.n_mob || m == j) continue;
+        const double dx = x[0] - S.px[m], dy = x[1] - S.py[m], dz = x[2] - S.pz[m];
+        hit = (dx * dx + dy * dy) + dz * dz <= S.hc2;
+      }
+    } else {
+      stack[top++] = root.x;
+    }
+    for (int guard = 0; top > 0 && !hit && guard < (1 << 22); ++guard) {
+      const int g = stack[--top];
+      for (int o = 0; o < 8 && !hit; ++o) {
+        const int nd = g + o;
+        const int4 b = S.nB[nd];
+        if ((b.z == 0 && b.w == 0) || b.y == 0) continue;
+        const float4 c = S.nA[nd];
+        double e2 = 0.0;  // squared distance from x to the box (FP64, exact enough for pruning)
+        for (int k = 0; k < 3; ++k) {
+          const double ck = k == 0 ? c.x : (k == 1 ? c.y : c.z);
+          const double e = fmax(fabs(x[k] - ck) - (double)c.w, 0.0);
+          e2 += e * e;
+        }
+        if (e2 > S.hc2 * (1.0 + 1e-9)) continue;
+        if (b.x >= 0) {
+          if (top < kStack) stack[top++] = b.x;
+          else atomicOr(&flags[3], 1);  // stack bound (never reached for valid trees)
+          continue;
+        }
+        for (int k = 0; k < b.y && !hit; ++k) {
+          const int m = __float_as_int(S.sB[nd * (S.C + 2) + k].w);
+          if (m >= S.n_mob || m == j) continue;
+          const double dx = x[0] - S.px[m], dy = x[1] - S.py[m], dz = x[2] - S.pz[m];
+          hit = (dx * dx + dy * dy) + dz * dz <= S.hc2;
+        }
+      }
+    }
+    if (hit) atomicOr(&flags[1], 1);
+  }
+}
+
 // Evaluation coefficients of every cluster in use (FP32 traversal).
 __global__ void k_wmirror(SysDev S, int n_nodes) {
   const long long total = (long long)n_nodes * S.K;
@@ -365,6 +418,10 @@ cudaError_t build_leaves_moments(const SysDev& S, int n_nodes, const int* perm, 
 }
 cudaError_t launch_wmirror(const SysDev& S, cudaStream_t st) {
   k_wmirror<<<grid_for((long long)S.node_cap * S.K, 256), 256, 0, st>>>(S, S.node_cap);
+  return cudaGetLastError();
+}
+cudaError_t launch_hard_core_check(const SysDev& S, int* flags, cudaStream_t st) {
+  if (S.hc2 > 0.0 && S.n_mob > 0) k_hard_core_check<<<grid_for(S.n_mob, 128), 128, 0, st>>>(S, flags);
   return cudaGetLastError();
 }
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st) {

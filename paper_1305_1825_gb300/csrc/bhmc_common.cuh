@@ -45,6 +45,8 @@ struct SysDev {
   double rmin2, rmax2;      // rmin * rmin, rmax * rmax (FP64 products)
   double img_R, img_alpha;
   double img_R2;            // img_R * img_R
+  double hc2;               // hard-core diameter squared (0: none), Eq. (2.1)
+  float hc2f;
   // charges
   double *px, *py, *pz, *pq;
   unsigned long long* ckey;

@@ -32,6 +32,7 @@ struct MoveSh : MoveSetup {
   int merge_d[2];          // topmost level to merge on each old path
   int cnt[BHMC_MAX_WARPS][5];
   int go;
+  int hc_hit;              // gradient traversal: hard-core overlap at point 1
   double xi[3];            // Langevin proposals: normal variates
   double U[2], gU[2][3];   // single-ion energy and gradient at the old / new position
   double tphi[2], tgrad[2][3];  // per-role potential and gradient of the last gradient traversal
@@ -316,6 +317,10 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
       s += pb - pa;
     }
     sh.dE = S.lB * s;
+    if (o.overlap) {  // hard core (Eq. 2.1): rejected as before evaluation
+      sh.outcome = BHMC_REJECT_OVERLAP;
+      sh.dE = 0.0;
+    }
   }
   __syncthreads();
 }
@@ -735,7 +740,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
       complete_paths(S, sh);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && sh.outcome < 0) {
       int acc, fl;
       metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
       sh.flagged = fl;
@@ -794,6 +799,7 @@ __device__ bool eval_grad(const SysDev& S, MoveStore& st, unsigned pmask) {
       for (int c = 0; c < 3; ++c) sh.tgrad[r][c] = o.grad[r][c];
     }
     sh.cnt[0][4] = o.err;
+    sh.hc_hit = o.overlap;
   }
   __syncthreads();
   return sh.cnt[0][4] == 0;
@@ -871,7 +877,10 @@ __device__ int mala_move(const SysDev& S, MoveStore& st, unsigned long long m, u
     }
     complete_paths(S, sh);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && sh.hc_hit) {  // hard core (Eq. 2.1) at the trial position
+      sh.outcome = BHMC_REJECT_OVERLAP;
+      sh.dE = 0.0;
+    } else if (threadIdx.x == 0) {
       ion_energy(S, sh, sh.b, sh.bi, sh.qb_img, sh.U[1], sh.gU[1]);
       sh.dE = sh.U[1] - sh.U[0];
       const double tb = tau * S.beta;
@@ -950,8 +959,10 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_delta(SysDev S, int i, 
   if (st.sh.outcome >= 0) return;
   eval_move<P, Real, LAYOUT>(S, st, false);
   if (threadIdx.x == 0) {
+    const bool hit = st.sh.outcome >= 0;  // hard-core overlap at the trial point
+    out->status = hit ? BHMC_EOVERLAP : 0;
     out->dE = st.sh.dE;
-    for (int k = 0; k < 4; ++k) out->cnt[k] = st.sh.cnt[0][k];
+    for (int k = 0; k < 4; ++k) out->cnt[k] = hit ? 0 : st.sh.cnt[0][k];
     out->err = st.sh.cnt[0][4];
   }
 }

@@ -34,6 +34,7 @@ struct TravPts {
 
 struct TravOut {
   double sum;
+  int overlap;    // the trial point (point 1) lies within the hard core of a mobile ion
   // gradient traversals: potential and its gradient per role, role 0 the
   // points 0 and 1 (ion), role 1 the points 2 and 3 (image); a traversal
   // evaluates at most one point of each role
@@ -427,6 +428,34 @@ __device__ __forceinline__ void direct_slot(const SysDev& S, const TravPts& T, f
     }
     ++pairs;
   }
+}
+
+// Hard core of Eq. (2.1) at the trial position (point 1): the slot's charge,
+// if a mobile ion other than the moved one, lies within the diameter.  FP32
+// float-pair distances settle it outside a 2^-16 band around the contact
+// distance; inside the band, the FP64 test of the definition.
+__device__ __forceinline__ bool hc_slot(const SysDev& S, const TravPts& T, float4 sa, float4 sb) {
+  const int j = __float_as_int(sb.w);
+  if (j >= S.n_mob || j == T.excl[0]) return false;
+  const float dx = (sa.x - T.hi[1][0]) + (sb.x - T.lo[1][0]);
+  const float dy = (sa.y - T.hi[1][1]) + (sb.y - T.lo[1][1]);
+  const float dz = (sa.z - T.hi[1][2]) + (sb.z - T.lo[1][2]);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 > S.hc2f * 1.0000153f) return false;
+  if (r2 < S.hc2f * 0.9999847f) return true;
+  const double ex = __dsub_rn(T.x[1][0], S.px[j]), ey = __dsub_rn(T.x[1][1], S.py[j]);
+  const double ez = __dsub_rn(T.x[1][2], S.pz[j]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= S.hc2;
+}
+
+// Whether the cluster box {centre, h} comes within the hard-core diameter of
+// point 1 (conservative: a box that does is never reported as out of reach).
+__device__ __forceinline__ bool hc_box(const SysDev& S, const TravPts& T, float4 a) {
+  const float4 h = T.h4[1], l = T.l4[1];
+  const float ex = fmaxf(fabsf((a.x - h.x) - l.x) - a.w, 0.f);
+  const float ey = fmaxf(fabsf((a.y - h.y) - l.y) - a.w, 0.f);
+  const float ez = fmaxf(fabsf((a.z - h.z) - l.z) - a.w, 0.f);
+  return ex * ex + ey * ey + ez * ez <= S.hc2f * 1.001f;
 }
 
 }  // namespace bhmc

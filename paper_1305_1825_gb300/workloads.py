@@ -138,6 +138,33 @@ def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8)
                 step=1.0, seed=seed)
 
 
+def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int = 8) -> dict:
+    """The electric double layer of Sec. 4 with its hard cores (Eq. 2.1): n
+    counterions of valence 2 and diameter 4 around a fixed macroion of radius
+    30 and valence -2n in a cell of radius 80, l_B = 7.14.  Ion centres lie in
+    [32, 78] (contact with the macroion and the cell wall), placed one by one
+    uniformly in that shell, each redrawn until it is farther than 4 from all
+    ions placed before (random sequential addition)."""
+    rng = np.random.default_rng(seed)
+    a, rcell, tau = 30.0, 80.0, 4.0
+    rmin, rmax = a + tau / 2, rcell - tau / 2
+    xyz = np.zeros((n, 3))
+    for k in range(n):
+        while True:
+            r = (rng.uniform(rmin ** 3, rmax ** 3)) ** (1.0 / 3.0)
+            x = r * _unit_vectors(rng, 1)[0]
+            if k == 0 or np.min(np.sum((xyz[:k] - x) ** 2, axis=1)) > tau * tau * (1.0 + 1e-12):
+                break
+        xyz[k] = x
+    lo, side = root_for(rcell)
+    params = base_params(lB=7.14, theta=theta, p=p, C=C, root_lo=lo, root_side=side,
+                         shell=(rmin, rmax), hard_core=tau)
+    q = np.concatenate([np.full(n, 2.0), [-2.0 * n]])
+    xyz = np.concatenate([xyz, np.zeros((1, 3))], axis=0)
+    return dict(name="edl-hard-N%d" % n, params=params, q=q, xyz=xyz, n_mobile=n, n_fixed=1,
+                step=2.0, seed=seed)
+
+
 def colloid_scaled(n: int = 100000, seed: int = 7, theta: float = 0.5, p: int = 4) -> dict:
     """The colloid radial law scaled to n ions: lengths R and r_max times
     s = (n / 1e4)^(1/3), macroion charge Z times s^2 (nearest value with n - |Z|

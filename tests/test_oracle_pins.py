@@ -426,3 +426,55 @@ def test_mala_samples_boltzmann_one_ion(oracle_mod):
         batches = f(r).reshape(100, -1).mean(axis=1)
         z = (batches.mean() - want) / (batches.std(ddof=1) / 10)
         assert abs(z) < 5, (want, batches.mean(), z)
+
+
+# ---------------------------------------------------------------- hard cores (Eq. 2.1)
+def test_hard_core_contact_rule(oracle_mod):
+    """A trial position at distance exactly tau from another mobile ion is
+    rejected (the pair potential is infinite for r <= tau); just beyond is not."""
+    tau = 1.5
+    params = W.base_params(hard_core=tau, root_lo=(-8.0,) * 3, root_side=16.0)
+    xyz = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0], [-3.0, 1.0, 0.0]])
+    s = oracle_mod.System(params, np.array([1.0, -1.0, 1.0]), xyz, 3, 0)
+    assert s.delta_energy(0, [3.0 - tau, 0.0, 0.0]).status == oracle_mod.EOVERLAP
+    assert s.delta_energy(0, [3.0 - tau - 1e-9, 0.0, 0.0]).status == 0
+    assert s.delta_energy(0, [0.5, 0.5, 0.5]).status == 0
+    # the moved ion itself never blocks its own move
+    assert s.delta_energy(1, [3.0 + 0.1, 0.0, 0.0]).status == 0
+    with pytest.raises(Exception):  # an initial overlap is refused
+        oracle_mod.System(params, np.array([1.0, 1.0]), np.array([[0.0, 0, 0], [1.0, 0, 0]]), 2, 0)
+
+
+def test_hard_core_chain_samples_excluded_volume(oracle_mod):
+    """Two neutral hard spheres of diameter tau in a ball of radius R: the chain
+    samples the uniform measure on non-overlapping pairs, so the pair distance
+    has density f(r) = 3r^2/R^3 - 9r^3/(4R^4) + 3r^5/(16R^6) (two uniform
+    points in a ball) restricted to r > tau."""
+    R, tau = 2.0, 1.0
+    params = W.base_params(hard_core=tau, shell=(0.0, R), root_lo=(-4.0,) * 3, root_side=8.0)
+    xyz = np.array([[1.0, 0.0, 0.0], [-1.0, 0.0, 0.0]])
+    s = oracle_mod.System(params, np.zeros(2), xyz, 2, 0)
+    recs = s.mc_run(seed=91, n_moves=400000, step=1.5)
+    assert not np.any(recs["outcome"] == 1)  # neutral: no energy rejections
+    pos = xyz.copy()
+    d = np.empty(len(recs))
+    for t, rec in enumerate(recs):
+        if rec["outcome"] == 0:
+            pos[rec["i"]] = rec["r_new"]
+        d[t] = np.linalg.norm(pos[0] - pos[1])
+    assert d.min() > tau
+    grid = np.linspace(tau, 2 * R, 200001)
+    f = 3 * grid ** 2 / R ** 3 - 9 * grid ** 3 / (4 * R ** 4) + 3 * grid ** 5 / (16 * R ** 6)
+    for g in (lambda v: v, lambda v: v * v):
+        want = np.trapezoid(g(grid) * f, grid) / np.trapezoid(f, grid)
+        batches = g(d).reshape(100, -1).mean(axis=1)
+        z = (batches.mean() - want) / (batches.std(ddof=1) / 10)
+        assert abs(z) < 5, (want, batches.mean(), z)
+
+
+def test_edl_hard_initial_configuration(oracle_mod):
+    wl = W.edl_hard(n=300, seed=2)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    q, x = s.charges()
+    d2 = np.sum((x[:300, None, :] - x[None, :300, :]) ** 2, axis=2) + np.eye(300) * 1e9
+    assert d2.min() > 16.0
