@@ -395,8 +395,9 @@ def _de_errors(bh, wl, n, seed, warps, layout):
 def _plain_moves(bh, wl, warps, layout, moves, precision=0):
     import torch
     ctx = bh.Context(wl, warps=warps, layout=layout, precision=precision)
-    ctx.step_mc(20, 1.0, seed=wl.get("seed", 1), move0=0)
-    ms, _ = _ev_time(lambda: ctx.step_mc(moves, 1.0, seed=wl.get("seed", 1), move0=20))
+    step = wl.get("step", 1.0)
+    ctx.step_mc(20, step, seed=wl.get("seed", 1), move0=0)
+    ms, _ = _ev_time(lambda: ctx.step_mc(moves, step, seed=wl.get("seed", 1), move0=20))
     ctx.close()
     torch.cuda.synchronize()
     return moves / (ms / 1e3)
@@ -404,8 +405,9 @@ def _plain_moves(bh, wl, warps, layout, moves, precision=0):
 
 def _batched_moves(bh, systems, seeds, warps, layout, moves):
     b = bh.Batch(systems, warps=warps, layout=layout)
-    b.step_mc(moves // 4, 1.0, seeds)
-    ms, st = _ev_time(lambda: b.step_mc(moves, 1.0, seeds, move0=moves // 4))
+    step = systems[0].get("step", 1.0)
+    b.step_mc(moves // 4, step, seeds)
+    ms, st = _ev_time(lambda: b.step_mc(moves, step, seeds, move0=moves // 4))
     acc = sum(s["accepted"] for s in st) / max(sum(s["moves"] for s in st), 1)
     b.close()
     return len(systems) * moves / (ms / 1e3), acc
@@ -416,7 +418,7 @@ def _oracle_moves(wl, seed, moves, budget_s):
     ref = oracle.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
     done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        ref.mc_run(seed, moves, m0=done)
+        ref.mc_run(seed, moves, step=wl.get("step", 1.0), m0=done)
         done += moves
     return done / (time.perf_counter() - t0)
 
@@ -508,6 +510,19 @@ def run_suite(args):
                   "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 2, 100, 2.0),
                   "dE_error": _de_errors(bh, wl, 40, 100 + p, args.warps, bh.LAYOUT_AOS)})
             del systems
+
+    # the paper's electric double layer with hard cores (Sec. 4, Eq. 2.1)
+    for n, reps in ((800, 152), (10000, 16)):
+        wl = W.edl_hard(n=n, seed=8)
+        rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400 if n > 1000 else 1000)
+        systems = [W.edl_hard(n=n, seed=8000 + r) for r in range(reps)]
+        rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps, bh.LAYOUT_AOS,
+                                     1000 if n <= 1000 else 400)
+        del systems
+        emit({"suite": "edl-hard-N%d" % n, "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
+              "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
+              "acceptance": acc,
+              "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
 
     # Langevin moves on the 1e4 colloid (step 0.05)
     wl = W.colloid(n=10000, seed=2)

@@ -149,13 +149,18 @@ def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int
     a, rcell, tau = 30.0, 80.0, 4.0
     rmin, rmax = a + tau / 2, rcell - tau / 2
     xyz = np.zeros((n, 3))
+    cells = {}  # cell list of side tau: a conflict can only lie in the 27 cells around
     for k in range(n):
         while True:
             r = (rng.uniform(rmin ** 3, rmax ** 3)) ** (1.0 / 3.0)
             x = r * _unit_vectors(rng, 1)[0]
-            if k == 0 or np.min(np.sum((xyz[:k] - x) ** 2, axis=1)) > tau * tau * (1.0 + 1e-12):
+            c = tuple(np.floor(x / tau).astype(int))
+            near = [m for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)
+                    for m in cells.get((c[0] + dx, c[1] + dy, c[2] + dz), ())]
+            if not near or np.min(np.sum((xyz[near] - x) ** 2, axis=1)) > tau * tau * (1.0 + 1e-12):
                 break
         xyz[k] = x
+        cells.setdefault(c, []).append(k)
     lo, side = root_for(rcell)
     params = base_params(lB=7.14, theta=theta, p=p, C=C, root_lo=lo, root_side=side,
                          shell=(rmin, rmax), hard_core=tau)
