@@ -483,12 +483,21 @@ static __device__ void move_slots(const SysDev& S, MoveSh& sh) {
   }
 }
 
-// Local adjustment (Sec. 3.3) of an accepted move, all threads of the block.
-// Requires complete paths and leaf counts (complete_paths).
-static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
+// Barrier of the first n threads: the whole block (bar 0) or a named barrier.
+__device__ __forceinline__ void team_sync(int bar, int n) {
+  if (bar == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+}
+
+// Local adjustment (Sec. 3.3) of an accepted move.  Requires complete paths
+// and leaf counts (complete_paths).  The first nt threads of the block (all
+// when nt == 0) run it, synchronised by barrier `bar` (0: __syncthreads).
+static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt = 0, int bar = 0) {
   MoveSh& sh = st.sh;
   const int K = S.K, SC = S.C + 2, P = S.p;
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x, nth = nt > 0 ? nt : (int)blockDim.x;
   constexpr int NL = BHMC_MAX_D + 1;
   // (A0) powers (r - r_A)^k along both paths of both moved charges (FP64,
   // built by repeated multiplication as in the definition of the moments)
@@ -514,7 +523,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
   if (tid == 0) sh.slot_i = S.slot_of[sh.i];
   if (tid == 1 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
   if (tid < 2) sh.merge_d[tid] = 1 << 20;
-  __syncthreads();
+  team_sync(bar, nth);
   // (A1) FP64 moments per level, both moved charges in one pass: for each
   // (level, term) the ion's update, then the image's (their paths share
   // clusters, and a cluster belongs to one level, so one thread owns each
@@ -568,7 +577,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
         if (nb >= 0) atomicAdd(count_ptr(S, nb), 1);
       }
     }
-    __syncthreads();
+    team_sync(bar, nth);
   }
   // (C) merge the topmost internal cluster on an old path holding <= C charges
   for (int it = tid; it < sh.nmov * NL; it += nth) {
@@ -577,7 +586,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
     const int4 b = S.nB[sh.path[2 * m][d]];
     if (b.x >= 0 && b.y <= S.C) atomicMin(&sh.merge_d[m], d);
   }
-  __syncthreads();
+  team_sync(bar, nth);
   if (tid == 0) {
     const int d0 = sh.merge_d[0];
     if (d0 < NL) merge_cluster(S, sh, sh.path[0][d0]);
@@ -587,7 +596,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
       if (d1 < NL && !inside) merge_cluster(S, sh, sh.path[2][d1]);
     }
   }
-  __syncthreads();
+  team_sync(bar, nth);
   // (D) split the new leaves while they hold more than C charges.  Without a
   // merge the new leaves' counts follow from the pre-move counts.
   bool may_split = true;
@@ -645,7 +654,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
           }
         }
       }
-      __syncthreads();
+      team_sync(bar, nth);
       if (sh.split_node < 0) break;
       for (int it = tid; it < 8 * K; it += nth) {
         const int o = it / K, t = it - o * K;
@@ -662,7 +671,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st) {
         S.M64[(size_t)ch * K + t] = M;
         mirror(S, ch, t, M);
       }
-      __syncthreads();
+      team_sync(bar, nth);
     }
   }
 }
@@ -695,20 +704,20 @@ struct MoveRec {
   int outcome, flagged;
 };
 
-// Barrier of warps 1-3 (the lookahead setup of the next move).
+// Barrier of warps 5-7 (the lookahead setup of the next move).
 __device__ __forceinline__ void bar_ahead() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
 
 // One full trial move m of a chain (all threads).  Returns the outcome, or -1
-// after a device error (recorded in S.err).  With `ahead` (blocks of at least
-// four warps), warps 1-3 set up move m + 1 into sh.nxt while move m is
-// decided; move m + 1 uses it unless move m moved the same ion (the setup
-// reads nothing else that a move changes), so the chain is unchanged.
+// after a device error (recorded in S.err).  With `ahead` (blocks of eight
+// warps), warps 5-7 set up move m + 1 into sh.nxt while warps 0-4 decide and
+// commit move m; move m + 1 uses it unless move m moved the same ion (the
+// setup reads nothing else that a move changes), so the chain is unchanged.
 template <int P, typename Real, int LAYOUT>
 __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica,
                        uint2 key, double step, MoveRec* rec, bool ahead) {
   MoveSh& sh = st.sh;
   const int warp = threadIdx.x >> 5;
-  ahead = ahead && blockDim.x >= 128;
+  ahead = ahead && blockDim.x == 256;
   if (sh.nxt_m == m) {
     constexpr int n = (int)(sizeof(MoveSetup) / sizeof(int));
     int* dst = reinterpret_cast<int*>(static_cast<MoveSetup*>(&sh));
@@ -729,32 +738,34 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
       if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
       return -1;
     }
-    if (ahead && warp >= 1 && warp <= 3) {
-      propose(S, sh.nxt, m + 1, replica, key, step, 1);
+    if (ahead && warp >= 5) {
+      // warps 5-7: the next move's setup, while warps 0-4 decide and commit
+      propose(S, sh.nxt, m + 1, replica, key, step, 5);
       bar_ahead();
-      setup_roles(S, sh.nxt, 1);
+      setup_roles(S, sh.nxt, 5);
       bar_ahead();
-      setup_finish(S, sh.nxt, 1);
-      if (threadIdx.x == 32) sh.nxt_m = m + 1;
+      setup_finish(S, sh.nxt, 5);
+      if (threadIdx.x == 160) sh.nxt_m = m + 1;
     } else {
+      const int nt = ahead ? 160 : (int)blockDim.x, bar = ahead ? 2 : 0;
       complete_paths(S, sh);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && sh.outcome < 0) {
-      int acc, fl;
-      metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
-      sh.flagged = fl;
-      if (!acc)
-        sh.outcome = BHMC_REJECT_ENERGY;
-      else if (capacity_violation(S, sh))
-        sh.outcome = BHMC_REJECT_CAPACITY;
-      else
-        sh.outcome = BHMC_ACCEPT;
-    }
-    __syncthreads();
-    if (sh.outcome == BHMC_ACCEPT) {
-      commit_move_block(S, st);
-      if (threadIdx.x == 0) *S.energy += sh.dE;
+      team_sync(bar, nt);
+      if (threadIdx.x == 0 && sh.outcome < 0) {
+        int acc, fl;
+        metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
+        sh.flagged = fl;
+        if (!acc)
+          sh.outcome = BHMC_REJECT_ENERGY;
+        else if (capacity_violation(S, sh))
+          sh.outcome = BHMC_REJECT_CAPACITY;
+        else
+          sh.outcome = BHMC_ACCEPT;
+      }
+      team_sync(bar, nt);
+      if (sh.outcome == BHMC_ACCEPT) {
+        commit_move_block(S, st, nt, bar);
+        if (threadIdx.x == 0) *S.energy += sh.dE;
+      }
     }
   }
   if (threadIdx.x == 0) {
