@@ -28,7 +28,7 @@ METRIC = "MC moves/sec at N=1e4..1e6 (batched vs plain, 1 GB300); dE rel err vs 
 UNIT = "moves/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -46,7 +46,11 @@ def parse():
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per workload family instead of the headline line")
     ap.add_argument("--suite-large", action="store_true", help="include the 1e6-ion items in --suite")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def parse_args(argv):
+    return parse(argv)
 
 
 def dist_env():
@@ -131,6 +135,22 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(ms, dist, device):
+    """The timed region's length: the maximum over ranks (every rank's replicas
+    must finish)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(reps, moves, steps, world, ms):
+    """Whole-job moves/s: every rank runs its own replicas (weak scaling)."""
+    return reps * moves * steps * world / (ms / 1e3)
 
 
 def workload(args, rank=0):
@@ -282,13 +302,8 @@ def run_gpu(args):
             tot += sum(s["moves"] for s in stats)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    moves_total = args.reps * args.moves * args.steps * world
-    value = moves_total / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    value = weak_value(args.reps, args.moves, args.steps, world, ms)
     acc_rate = acc / max(tot, 1)
 
     # end to end through the public call (host clock): seeds up, stats down, every step
