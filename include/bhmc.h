@@ -162,6 +162,16 @@ bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t 
 bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t seed, uint64_t move0,
                            bhmc_mc_stats* stats, bhmc_move_record* records);
 
+/* Radial distribution of the mobile ions (Sec. 4: RDF g(r) and ICDF Q(r) of
+   the double layer): for every mobile ion with r_lo <= r < r_hi, r = sqrt((x x
+   + y y) + z z) in FP64, bin k = floor((r - r_lo) / ((r_hi - r_lo) / nbins)),
+   adds 1 to counts[k] and its charge to charge[k] (host arrays of nbins,
+   accumulated, so that calls between steps average over the chain).
+   BHMC_EINVAL for nbins outside [1, 2^24] or r_hi <= r_lo.  Not a call of the
+   paper; it measures its Fig. 6 quantities. */
+bhmc_status bhmc_radial_counts(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
+                               double* charge);
+
 /* Running energy (sum of accepted dE since creation, or rebased by set). */
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E);
 bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);
@@ -221,6 +231,10 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
 bhmc_status bhmc_batch_destroy(bhmc_batch* batch);
 /* Borrowed context of replica r (valid until the batch is destroyed; do not destroy it). */
 bhmc_status bhmc_batch_replica(bhmc_batch* batch, int32_t r, bhmc_ctx** ctx);
+/* bhmc_radial_counts summed over every replica of the batch. */
+bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
+                                     double* charge);
+
 /* n_moves Metropolis trials on every replica in ONE persistent kernel launch,
    replayed from a CUDA graph.  Replica r uses key seeds[r] and counter
    (m, r, tag).  stats: n_rep entries (may be NULL). */

@@ -84,6 +84,8 @@ def lib():
         L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                    C.POINTER(McStats), C.c_void_p]
         L.bhmc_energy_counters.argtypes = [C.c_void_p, _dp, C.POINTER(Counters)]
+        L.bhmc_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
+        L.bhmc_batch_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
         L.bhmc_step_mala.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                      C.POINTER(McStats), C.c_void_p]
         L.bhmc_get_energy.argtypes = [C.c_void_p, _dp]
@@ -223,6 +225,29 @@ def bhmc_energy_counters(h):
     c = Counters()
     _check(lib().bhmc_energy_counters(h, C.byref(e), C.byref(c)), "bhmc_energy_counters")
     return e.value, c
+
+
+def bhmc_radial_counts(h, counts, charge, r_lo, r_hi, batch=False):
+    """Adds the radial counts and charges of the mobile ions to the int64 and
+    float64 numpy arrays counts and charge (one entry per bin)."""
+    f = lib().bhmc_batch_radial_counts if batch else lib().bhmc_radial_counts
+    _check(f(h, len(counts), r_lo, r_hi, counts.ctypes.data_as(_i64p), charge.ctypes.data_as(_dp)),
+           "bhmc_radial_counts")
+
+
+def radial_profiles(counts, charge, r_lo, r_hi, samples, q_fixed=0.0):
+    """RDF and ICDF of Sec. 4 from accumulated radial counts: with <N_k> the
+    mean count of bin k (counts / samples) and V_k its shell volume,
+    g_k = (<N_k> / V_k) / sum_j (<N_j> / V_j) (the bins normalised to sum 1),
+    Q(r_k) = q_fixed + sum_{j <= k} <q N_j> at the outer edge r_k of bin k.
+    Returns (bin centres, g, outer edges, Q)."""
+    n = len(counts)
+    edges = np.linspace(r_lo, r_hi, n + 1)
+    vol = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    rho = counts / float(samples) / vol
+    g = rho / rho.sum()
+    Q = q_fixed + np.cumsum(charge / float(samples))
+    return 0.5 * (edges[1:] + edges[:-1]), g, edges[1:], Q
 
 
 def bhmc_energy_direct(h):
@@ -384,6 +409,9 @@ class Context:
     def energy_counters(self):
         return bhmc_energy_counters(self.h)
 
+    def radial_counts(self, counts, charge, r_lo, r_hi):
+        bhmc_radial_counts(self.h, counts, charge, r_lo, r_hi)
+
     def energy_direct(self):
         return bhmc_energy_direct(self.h)
 
@@ -427,6 +455,9 @@ class Batch:
 
     def step_mc(self, n_moves, step, seeds, move0=0):
         return bhmc_batch_step_mc(self.h, self.n, n_moves, step, seeds, move0)
+
+    def radial_counts(self, counts, charge, r_lo, r_hi):
+        bhmc_radial_counts(self.h, counts, charge, r_lo, r_hi, batch=True)
 
     def close(self):
         if self.h:

@@ -643,6 +643,50 @@ bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t
   return BHMC_OK;
 }
 
+// Radial counts of one or more systems into host arrays (accumulated).
+static bhmc_status radial_impl(bhmc_ctx* const* ctxs, int n, int32_t nbins, double r_lo, double r_hi,
+                               int64_t* counts, double* charge) {
+  if (!ctxs || n < 1 || nbins < 1 || nbins > (1 << 24) || !counts || !charge || !(r_hi > r_lo) ||
+      !std::isfinite(r_lo) || !std::isfinite(r_hi))
+    return BHMC_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    bhmc_status rc = ctx_check(ctxs[k]);
+    if (rc != BHMC_OK) return rc;
+  }
+  const double width = (r_hi - r_lo) / (double)nbins;
+  cudaStream_t st = ctxs[0]->stream;
+  unsigned long long* dc = nullptr;
+  double* dq = nullptr;
+  if (cudaMalloc(&dc, sizeof(unsigned long long) * nbins) != cudaSuccess) return BHMC_ENOMEM;
+  if (cudaMalloc(&dq, sizeof(double) * nbins) != cudaSuccess) {
+    cudaFree(dc);
+    return BHMC_ENOMEM;
+  }
+  std::vector<unsigned long long> hc(nbins);
+  std::vector<double> hq(nbins);
+  bool ok = cudaMemsetAsync(dc, 0, sizeof(unsigned long long) * nbins, st) == cudaSuccess &&
+            cudaMemsetAsync(dq, 0, sizeof(double) * nbins, st) == cudaSuccess;
+  for (int k = 0; ok && k < n; ++k)
+    ok = launch_radial_counts(ctxs[k]->S, nbins, r_lo, r_hi, width, dc, dq, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(hc.data(), dc, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost, st) ==
+                 cudaSuccess &&
+       cudaMemcpyAsync(hq.data(), dq, sizeof(double) * nbins, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(dc);
+  cudaFree(dq);
+  if (!ok) return BHMC_ECUDA;
+  for (int k = 0; k < nbins; ++k) {
+    counts[k] += (int64_t)hc[k];
+    charge[k] += hq[k];
+  }
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_radial_counts(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
+                               double* charge) {
+  return radial_impl(&ctx, 1, nbins, r_lo, r_hi, counts, charge);
+}
+
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E) {
   if (!ctx || !E) return BHMC_EINVAL;
   CK(cudaMemcpyAsync(E, ctx->S.energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -981,6 +1025,12 @@ bhmc_status bhmc_batch_replica(bhmc_batch* B, int32_t r, bhmc_ctx** ctx) {
   if (!B || !ctx || r < 0 || r >= (int32_t)B->reps.size()) return BHMC_EINVAL;
   *ctx = B->reps[r];
   return BHMC_OK;
+}
+
+bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
+                                     double* charge) {
+  if (!B) return BHMC_EINVAL;
+  return radial_impl(B->reps.data(), (int)B->reps.size(), nbins, r_lo, r_hi, counts, charge);
 }
 
 bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,

@@ -424,6 +424,27 @@ cudaError_t launch_hard_core_check(const SysDev& S, int* flags, cudaStream_t st)
   if (S.hc2 > 0.0 && S.n_mob > 0) k_hard_core_check<<<grid_for(S.n_mob, 128), 128, 0, st>>>(S, flags);
   return cudaGetLastError();
 }
+// Radial counts of the mobile ions (Sec. 4 RDF and ICDF): r = sqrt((x x + y y)
+// + z z), bin = floor((r - lo) / width), counted when 0 <= bin < nbins and
+// lo <= r < hi (FP64, this operation order).
+__global__ void k_radial_counts(SysDev S, int nbins, double lo, double hi, double width,
+                                unsigned long long* counts, double* charge) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_mob; j += gridDim.x * blockDim.x) {
+    const double x = S.px[j], y = S.py[j], z = S.pz[j];
+    const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    if (!(r >= lo && r < hi)) continue;
+    const double t = floor(__ddiv_rn(__dsub_rn(r, lo), width));
+    if (!(t >= 0.0 && t < (double)nbins)) continue;
+    const int k = (int)t;
+    atomicAdd(&counts[k], 1ULL);
+    atomicAdd(&charge[k], S.pq[j]);
+  }
+}
+cudaError_t launch_radial_counts(const SysDev& S, int nbins, double lo, double hi, double width,
+                                 unsigned long long* counts, double* charge, cudaStream_t st) {
+  if (S.n_mob > 0) k_radial_counts<<<grid_for(S.n_mob, 256), 256, 0, st>>>(S, nbins, lo, hi, width, counts, charge);
+  return cudaGetLastError();
+}
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st) {
   k_commit<<<1, 128, 0, st>>>(S, i, b[0], b[1], b[2], status);
   return cudaGetLastError();

@@ -18,6 +18,9 @@ cudaError_t build_leaves_moments(const SysDev& S, int n_nodes, const int* perm, 
 cudaError_t launch_wmirror(const SysDev& S, cudaStream_t st);
 // Sets flags[1] when two mobile ions of the built tree overlap (hard cores).
 cudaError_t launch_hard_core_check(const SysDev& S, int* flags, cudaStream_t st);
+// Adds the radial counts and charges of the mobile ions to counts[nbins], charge[nbins] (device).
+cudaError_t launch_radial_counts(const SysDev& S, int nbins, double lo, double hi, double width,
+                                 unsigned long long* counts, double* charge, cudaStream_t st);
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st);
 cudaError_t launch_direct_energy(const SysDev& S, double* partial, int nblk, cudaStream_t st);
 cudaError_t launch_interleave(const SysDev& S, double* q, double* xyz, cudaStream_t st);
