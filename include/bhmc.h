@@ -61,7 +61,7 @@ typedef struct {
   double lB;          /* Bjerrum length (> 0) */
   double beta;        /* inverse temperature of the Metropolis rule (>= 0) */
   double theta;       /* MAC: multipole iff rho_A/|r_A - x| <= theta, 0 <= theta < 1 */
-  int32_t p;          /* Taylor truncation order; the CUDA path supports 2, 4 and 6 */
+  int32_t p;          /* Taylor truncation order, 0..6 (the oracle goes to 10) */
   int32_t N0;         /* minimum expansion number (>= 0) */
   int32_t C;          /* leaf capacity, 2..32: a cluster holding more than C charges splits */
   int32_t Dmax;       /* deepest level, 1..20 */

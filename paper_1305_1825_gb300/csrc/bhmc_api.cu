@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "bhmc_build.cuh"
@@ -89,7 +90,7 @@ static bool pow2(double v) {
 static bhmc_status validate(const bhmc_params* P) {
   if (!P) return BHMC_EINVAL;
   if (!(P->lB > 0.0) || !(P->beta >= 0.0) || !(P->theta >= 0.0 && P->theta < 1.0)) return BHMC_EINVAL;
-  if (P->p != 2 && P->p != 4 && P->p != 6) return BHMC_EINVAL;
+  if (P->p < 0 || P->p > BHMC_MAX_P) return BHMC_EINVAL;
   if (P->N0 < 0 || P->C < 2 || P->C > BHMC_MAX_C || P->Dmax < 1 || P->Dmax > BHMC_MAX_D) return BHMC_EINVAL;
   if (!pow2(P->root_side)) return BHMC_EINVAL;
   const double hmin = std::ldexp(P->root_side, -P->Dmax);
@@ -181,6 +182,20 @@ static WMap wmap_make(int p) {
   return w;
 }
 static int wmap_nnz(int p) { return (int)wmap_make(p).col.size(); }
+
+// Calls f(std::integral_constant<int, p>{}) for the multipole order p (0..6).
+template <typename F>
+static auto by_p(int p, F&& f) {
+  switch (p) {
+    case 0: return f(std::integral_constant<int, 0>{});
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    default: return f(std::integral_constant<int, 6>{});
+  }
+}
 
 template <typename T>
 static T* carve(char*& cur, size_t n) {
@@ -520,11 +535,7 @@ bhmc_status bhmc_get_charges(bhmc_ctx* ctx, double* q, double* xyz, int32_t flag
 }
 
 static cudaError_t dispatch_delta(bhmc_ctx* c, int i, const double* b, DeltaOut* out) {
-  switch (c->P.p) {
-    case 2: return launch_delta<2>(c->S, c->P.warps, i, b, out, c->stream);
-    case 4: return launch_delta<4>(c->S, c->P.warps, i, b, out, c->stream);
-    default: return launch_delta<6>(c->S, c->P.warps, i, b, out, c->stream);
-  }
+  return by_p(c->P.p, [&](auto PC) { return launch_delta<PC.value>(c->S, c->P.warps, i, b, out, c->stream); });
 }
 
 bhmc_status bhmc_delta_energy(bhmc_ctx* ctx, int64_t i, const double r_new[3], double* dE,
@@ -567,11 +578,7 @@ bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]) {
 
 static cudaError_t dispatch_step(bhmc_ctx* c, unsigned long long m, unsigned long long seed, double step,
                                  MoveRec* rec, bhmc_mc_stats* st) {
-  switch (c->P.p) {
-    case 2: return launch_step<2>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
-    case 4: return launch_step<4>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
-    default: return launch_step<6>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream);
-  }
+  return by_p(c->P.p, [&](auto PC) { return launch_step<PC.value>(c->S, c->P.warps, m, 0u, seed, step, rec, st, c->stream); });
 }
 
 bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed, uint64_t move0,
@@ -622,11 +629,7 @@ bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t
   CK(cudaMemsetAsync(&dio->stats, 0, sizeof(bhmc_mc_stats), ctx->stream));
   for (uint64_t t = 0; t < n_moves; ++t) {
     cudaError_t e;
-    switch (ctx->P.p) {
-      case 2: e = launch_step_mala<2>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
-      case 4: e = launch_step_mala<4>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
-      default: e = launch_step_mala<6>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); break;
-    }
+    e = by_p(ctx->P.p, [&](auto PC) { return launch_step_mala<PC.value>(ctx->S, ctx->P.warps, move0 + t, 0u, seed, tau, drec ? drec + t : nullptr, &dio->stats, ctx->stream); });
     if (e != cudaSuccess) {
       cudaFree(drec);
       ctx->sticky = BHMC_ECUDA;
@@ -707,11 +710,7 @@ bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E) {
 static cudaError_t dispatch_energy(bhmc_ctx* c, int grid, double* partial, double* phi, int* err,
                                    unsigned long long* cnt) {
   const int w = BHMC_ENERGY_WARPS;
-  switch (c->P.p) {
-    case 2: return launch_energy<2>(c->S, w, grid, partial, phi, err, cnt, c->stream);
-    case 4: return launch_energy<4>(c->S, w, grid, partial, phi, err, cnt, c->stream);
-    default: return launch_energy<6>(c->S, w, grid, partial, phi, err, cnt, c->stream);
-  }
+  return by_p(c->P.p, [&](auto PC) { return launch_energy<PC.value>(c->S, w, grid, partial, phi, err, cnt, c->stream); });
 }
 
 static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_t flags,
@@ -816,11 +815,7 @@ bhmc_status bhmc_forces(bhmc_ctx* ctx, double* dEdr, double* dEdq, int32_t flags
   cudaError_t e = cudaMemsetAsync(lam, 0, sizeof(double) * (nl + 4 * n), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream);
   if (e == cudaSuccess) {
-    switch (ctx->P.p) {
-      case 2: e = launch_forces<2>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
-      case 4: e = launch_forces<4>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
-      default: e = launch_forces<6>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); break;
-    }
+    e = by_p(ctx->P.p, [&](auto PC) { return launch_forces<PC.value>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); });
   }
   if (e == cudaSuccess) e = launch_forces_push(S, phi, tg, lam, psi, src, odr, odq, ctx->stream);
   int herr = 0;
@@ -962,11 +957,7 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
     return BHMC_ECUDA;
   }
   int occ = 0;
-  switch (B->p) {
-    case 2: occ = batch_occupancy<2>(views[0], B->warps); break;
-    case 4: occ = batch_occupancy<4>(views[0], B->warps); break;
-    default: occ = batch_occupancy<6>(views[0], B->warps); break;
-  }
+  occ = by_p(B->p, [&](auto PC) { return batch_occupancy<PC.value>(views[0], B->warps); });
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -983,11 +974,7 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
   ok = ok && cudaMemsetAsync(B->d_next, 0, sizeof(int), cs) == cudaSuccess;
   cudaError_t le = cudaSuccess;
   if (ok) {
-    switch (B->p) {
-      case 2: le = launch_batch<2>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
-      case 4: le = launch_batch<4>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
-      default: le = launch_batch<6>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); break;
-    }
+    le = by_p(B->p, [&](auto PC) { return launch_batch<PC.value>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); });
   }
   ok = ok && le == cudaSuccess;
   ok = ok && cudaMemcpyAsync(B->h_stats, B->d_stats, sizeof(bhmc_mc_stats) * n_rep, cudaMemcpyDeviceToHost,

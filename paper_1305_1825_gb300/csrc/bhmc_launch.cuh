@@ -55,8 +55,12 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
   template <> cudaError_t launch_forces<P>(const SysDev&, int, double*, double*, double*, double*, double*, int*, \
                                            cudaStream_t);
 
+BHMC_EXTERN_P(0)
+BHMC_EXTERN_P(1)
 BHMC_EXTERN_P(2)
+BHMC_EXTERN_P(3)
 BHMC_EXTERN_P(4)
+BHMC_EXTERN_P(5)
 BHMC_EXTERN_P(6)
 
 }  // namespace bhmc

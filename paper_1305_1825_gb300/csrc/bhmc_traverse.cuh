@@ -255,7 +255,7 @@ __device__ __forceinline__ float w_multipole(const SysDev& S, int node, float rx
     const float sd = ux * dx + uy * dy + uz * dz, td = dx * dx + dy * dy + dz * dz;
     float q0 = 1.f, q1 = sd;
     pk[0] -= qe[e];
-    if (P >= 1) pk[1] += qe[e] * q1;
+    if constexpr (P >= 1) pk[1] += qe[e] * q1;
 #pragma unroll
     for (int k = 1; k < P; ++k) {
       const float q2 = ((2.f * k + 1.f) * sd * q1 - (float)k * td * q0) * (1.f / (k + 1.f));

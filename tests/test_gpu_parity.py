@@ -59,7 +59,7 @@ def test_build_matches_oracle(bh, oracle_mod, kind):
 
 
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
-@pytest.mark.parametrize("p", [2, 4, 6])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5, 6])
 def test_delta_energy_matches_oracle(bh, oracle_mod, theta, p):
     wl = W.colloid(n=2000, seed=5, theta=theta, p=p)
     ref = _oracle(oracle_mod, wl)
@@ -267,3 +267,22 @@ def test_potentials_sampled(bh, oracle_mod, p):
     for j in rng.choice(len(q), 150, replace=False):
         e = ref.phi(x[j], excl=[int(j)])
         assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
+
+
+@pytest.mark.parametrize("p", [0, 1, 3, 5])
+def test_chain_and_energy_every_order(bh, oracle_mod, p):
+    """Orders beyond the benchmark's: a batched chain (8 warps) and the full
+    energy against the oracle."""
+    wl = W.colloid(n=1500, seed=20 + p, p=p)
+    ref = _oracle(oracle_mod, wl)
+    batch = bh.Batch([wl], warps=8)
+    st = batch.step_mc(300, 1.0, [31])
+    orec = ref.mc_run(31, 300, replica=0)
+    flagged = int(orec["flagged"].sum())
+    assert abs(st[0]["accepted"] - int((orec["outcome"] == 0).sum())) <= flagged
+    if flagged == 0:
+        assert batch.replica(0).export_tree() == ref.export_tree()
+    ctx = bh.Context(wl, warps=4, layout=1)
+    ref0 = _oracle(oracle_mod, wl)
+    scale = float(np.abs(wl["q"]).sum())
+    assert abs(ctx.energy() - ref0.energy_tree()) <= 2e-6 * abs(ref0.energy_tree()) + 2e-6 * scale
