@@ -491,6 +491,7 @@ def run_suite(args):
     1e6-ion colloid, and Langevin moves.  Moves per second are CUDA-event times
     on the library's stream; dE errors are measured on the GPU against its FP64
     mode and the theta = 0 direct sum."""
+    import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -538,6 +539,52 @@ def run_suite(args):
               "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
               "acceptance": acc,
               "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
+
+    # error and speed against the multipole order (the paper's Figs. 5 and 7):
+    # Eq. (4.1) E = sqrt(sum_i |V_i - Vt_i|^2 / sum_i |V_i|^2) over the ions,
+    # V exact (theta = 0, FP64), Vt the FP32 treecode, on the double layer
+    for theta in (0.5, 0.3):
+        for pp in range(0, 7):
+            wl = W.edl_hard(n=800, seed=8, theta=theta, p=pp)
+            n = wl["n_mobile"]
+            exact_wl = dict(wl, params=dict(wl["params"], theta=0.0))
+            ex = bh.Context(exact_wl, precision=bh.PREC_F64, warps=8)
+            v = ex.potentials()[:n]
+            ex.close()
+            tr = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
+            vt = tr.potentials()[:n]
+            tr.close()
+            E = float(np.sqrt(np.sum((v - vt) ** 2) / np.sum(v ** 2)))
+            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 1000)
+            systems = [W.edl_hard(n=800, seed=8000 + r, theta=theta, p=pp) for r in range(152)]
+            rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps,
+                                       bh.LAYOUT_AOS, 1000)
+            del systems
+            emit({"suite": "p-sweep-edl-N800", "theta": theta, "p": pp, "E_eq4_1": E,
+                  "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b})
+    # the minimum expansion number N0 (Sec. 3.2): small clusters summed directly
+    for pp in (2, 4):
+        for n0 in (0, 4, 8, 16):
+            wl = W.edl_hard(n=800, seed=8, theta=0.5, p=pp)
+            wl["params"]["N0"] = n0
+            n = wl["n_mobile"]
+            ex = bh.Context(dict(wl, params=dict(wl["params"], theta=0.0)), precision=bh.PREC_F64, warps=8)
+            v = ex.potentials()[:n]
+            ex.close()
+            tr = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
+            vt = tr.potentials()[:n]
+            tr.close()
+            systems = []
+            for r in range(152):
+                w2 = W.edl_hard(n=800, seed=8000 + r, theta=0.5, p=pp)
+                w2["params"]["N0"] = n0
+                systems.append(w2)
+            rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps,
+                                       bh.LAYOUT_AOS, 1000)
+            del systems
+            emit({"suite": "N0-sweep-edl-N800", "theta": 0.5, "p": pp, "N0": n0,
+                  "E_eq4_1": float(np.sqrt(np.sum((v - vt) ** 2) / np.sum(v ** 2))),
+                  "gpu_batched_152_replicas_moves_per_s": rate_b})
 
     # Langevin moves on the 1e4 colloid (step 0.05)
     wl = W.colloid(n=10000, seed=2)
