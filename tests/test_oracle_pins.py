@@ -344,6 +344,27 @@ def test_relative_error_decreases_with_order(oracle_mod):
     assert errs[(0.5, 2)] < 0.01 and errs[(0.3, 2)] < 0.001
 
 
+
+def test_relative_error_on_equilibrated_hard_core_layer(oracle_mod):
+    """Eq. (4.1) over every charge, macroion included, on a snapshot of an
+    equilibrated chain of the Sec. 4 double layer with hard cores (Eq. 2.1):
+    below 1 % at theta = 0.5 and 0.1 % at theta = 0.3 for p = 2, falling with p."""
+    wl = W.edl_hard(n=800, seed=8)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    s.mc_run(3, 200000, step=wl["step"])
+    snap = s.charges()[1][:801].copy()
+    assert np.median(np.linalg.norm(snap[:800], axis=1)) < 40.0  # condensed at the surface
+    errs = {}
+    for theta in (0.3, 0.5):
+        for p in (1, 2, 3):
+            w = W.edl_hard(n=800, seed=8, theta=theta, p=p)
+            t = oracle_mod.System(w["params"], w["q"], snap, w["n_mobile"], w["n_fixed"])
+            vt, vd = t.potentials()
+            errs[(theta, p)] = math.sqrt(((vt - vd) ** 2).sum() / (vd ** 2).sum())
+    for theta in (0.3, 0.5):
+        assert errs[(theta, 1)] > errs[(theta, 2)] > errs[(theta, 3)]
+    assert errs[(0.5, 2)] < 0.01 and errs[(0.3, 2)] < 0.001
+
 # ---------------------------------------------------------------- adjoint (forces)
 def test_forces_euler_identity_and_finite_differences(oracle_mod):
     """E_tree is a quadratic form in the charges: sum_k q_k dE/dq_k = 2E exactly;
