@@ -488,6 +488,7 @@ def _field_item(bh, name, wl, reps=3):
 def _eq4_1(bh, wl, warps):
     """Eq. (4.1) relative error of the FP32 treecode against the exact sum (theta = 0,
     FP64): V_i = q_i phi_i over every charge, and over the mobile ions alone."""
+    import numpy as np
     n, nt = wl["n_mobile"], wl["n_mobile"] + wl["n_fixed"]
     ex = bh.Context(dict(wl, params=dict(wl["params"], theta=0.0)), precision=bh.PREC_F64, warps=8)
     v = ex.potentials()[:nt] * np.asarray(wl["q"][:nt])
@@ -541,18 +542,22 @@ def run_suite(args):
                   "dE_error": _de_errors(bh, wl, 40, 100 + p, args.warps, bh.LAYOUT_AOS)})
             del systems
 
-    # the paper's electric double layer with hard cores (Sec. 4, Eq. 2.1)
+    # the paper's electric double layer with hard cores (Sec. 4, Eq. 2.1), on
+    # the adaptive tree and on the fixed-level tree of Sec. 3.2 (L_max = 6:
+    # leaves of side tau)
     for n, reps in ((800, 152), (10000, 16)):
-        wl = W.edl_hard(n=n, seed=8)
-        rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400 if n > 1000 else 1000)
-        systems = [W.edl_hard(n=n, seed=8000 + r) for r in range(reps)]
-        rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps, bh.LAYOUT_AOS,
-                                     1000 if n <= 1000 else 400)
-        del systems
-        emit({"suite": "edl-hard-N%d" % n, "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
-              "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
-              "acceptance": acc,
-              "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
+        for Lmax in (0, 6):
+            wl = W.edl_hard(n=n, seed=8, Lmax=Lmax)
+            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400 if n > 1000 else 1000)
+            systems = [W.edl_hard(n=n, seed=8000 + r, Lmax=Lmax) for r in range(reps)]
+            rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps,
+                                         bh.LAYOUT_AOS, 1000 if n <= 1000 else 400)
+            del systems
+            emit({"suite": "edl-hard-N%d" % n, "tree": "fixed L_max=%d" % Lmax if Lmax else "adaptive C=8",
+                  "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
+                  "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
+                  "acceptance": acc,
+                  "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
 
     # error and speed against the multipole order (the paper's Figs. 5 and 7):
     # Eq. (4.1) E = sqrt(sum_i |V_i - Vt_i|^2 / sum_i |V_i|^2) over the ions,

@@ -63,7 +63,8 @@ typedef struct {
   double theta;       /* MAC: multipole iff rho_A/|r_A - x| <= theta, 0 <= theta < 1 */
   int32_t p;          /* Taylor truncation order, 0..6 (the oracle goes to 10) */
   int32_t N0;         /* minimum expansion number (>= 0) */
-  int32_t C;          /* leaf capacity, 2..32: a cluster holding more than C charges splits */
+  int32_t C;          /* leaf capacity, 2..32: a cluster holding more than C charges splits (more
+                         than 0 with fixed_depth); no depth-Dmax cell may hold more than C */
   int32_t Dmax;       /* deepest level, 1..20 */
   double root_lo[3];  /* lower corner of the root cube, a multiple of side/2^Dmax */
   double root_side;   /* side of the root cube, a power of two */
@@ -74,11 +75,15 @@ typedef struct {
   int32_t precision;  /* BHMC_PREC_F32 (FP32 traversal, FP64 moments) or BHMC_PREC_F64 (all FP64) */
   int32_t warps;      /* warps cooperating on one move: 1, 2, 4 or 8 */
   int32_t layout;     /* BHMC_LAYOUT_SOA or BHMC_LAYOUT_AOS for the FP32 moment mirror */
-  double node_factor; /* node pool = 64 + node_factor * charges (0 selects 2.0) */
+  double node_factor; /* node pool = 64 + node_factor * charges (0 selects 1 + max(1, 8/C), or
+                         8 (Dmax - floor(log8 charges) + 1) with fixed_depth) */
   double hard_core;   /* common diameter tau of the mobile ions (Eq. 2.1: the pair potential is
                          infinite for r_ij <= tau); a trial position within tau of another mobile
                          ion is rejected (BHMC_REJECT_OVERLAP); 0 disables.  Images and fixed
                          charges carry no hard core (the macroion's is the shell). */
+  int32_t fixed_depth; /* 1: the fixed-level tree of Sec. 3.2 with L_max = Dmax (every non-empty
+                          cluster above Dmax is bisected, so all charges sit in depth-Dmax
+                          leaves); 0: the adaptive tree of leaf capacity C */
 } bhmc_params;
 
 typedef struct bhmc_ctx bhmc_ctx;

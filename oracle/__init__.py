@@ -44,6 +44,7 @@ class Params(C.Structure):
         ("shell", C.c_int32), ("shell_rmin", C.c_double), ("shell_rmax", C.c_double),
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
         ("hard_core", C.c_double),
+        ("fixed_depth", C.c_int32),
     ]
 
 
@@ -175,6 +176,7 @@ def make_params(d: dict) -> Params:
     P.images = 1 if d.get("image") else 0
     P.image_R, P.image_alpha = (d["image"] if d.get("image") else (0.0, 0.0))
     P.hard_core = d.get("hard_core", 0.0) or 0.0
+    P.fixed_depth = 1 if d.get("fixed_depth", False) else 0
     return P
 
 
@@ -303,12 +305,16 @@ class System:
     def export_tree(self):
         """{(depth, key): (is_leaf, count, members-tuple or None)}"""
         cap = 8 * self.n_charges + 64
-        rows = np.zeros((cap, 4), dtype=np.int64)
         mem = np.zeros(self.n_charges + 8, dtype=np.int64)
-        n = lib().or_export_tree(self._h, rows.ctypes.data_as(_i64p), cap,
-                                 mem.ctypes.data_as(_i64p), len(mem))
-        if n < 0:
-            raise RuntimeError("export buffer too small")
+        while True:  # deep (fixed-level) trees hold more clusters than charges
+            rows = np.zeros((cap, 4), dtype=np.int64)
+            n = lib().or_export_tree(self._h, rows.ctypes.data_as(_i64p), cap,
+                                     mem.ctypes.data_as(_i64p), len(mem))
+            if n >= 0:
+                break
+            if cap > 64 * (self.n_charges + 64) * 21:
+                raise RuntimeError("export buffer too small")
+            cap *= 4
         out = {}
         off = 0
         for d, k, leaf, cnt in rows[:n]:

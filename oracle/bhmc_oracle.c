@@ -335,9 +335,14 @@ static void split_node(or_sys* s, int a) {
   for (int o = 0; o < 8; ++o) node_moments(s, g + o);
 }
 
+/* A cluster above Dmax splits when it holds more than this many charges: C,
+   or 0 for the fixed-level tree of Sec. 3.2 (every non-empty cluster is
+   bisected down to L_max = Dmax). */
+static int split_threshold(const or_params* P) { return P->fixed_depth ? 0 : P->C; }
+
 static void split_rec(or_sys* s, int a) {
   or_node* A = &s->nodes[a];
-  if (A->n > s->P.C && A->depth < s->P.Dmax) {
+  if (A->n > split_threshold(&s->P) && A->depth < s->P.Dmax) {
     split_node(s, a);
     int g = s->nodes[a].child;
     for (int o = 0; o < 8; ++o) split_rec(s, g + o);
@@ -795,20 +800,20 @@ int or_commit_move(or_sys* s, int64_t i, const double b[3]) {
     for (int d = 0; d < s->L; ++d) old_path[t][d] = *track_node(s, m.excl[t], d);
   move_charge(s, i, m.b, m.q);
   if (s->P.images) move_charge(s, m.excl[1], m.bi, m.qb_img);
-  /* merge the topmost internal cluster on an old path holding at most C charges */
+  /* merge the topmost internal cluster on an old path holding no more charges than the split threshold */
   for (int t = 0; t < m.n_excl; ++t) {
     for (int d = 0; d < s->L; ++d) {
       int a = old_path[t][d];
       if (a < 0) break;
       or_node* A = &s->nodes[a];
       if (!A->alive) break;
-      if (A->child >= 0 && A->n <= s->P.C) {
+      if (A->child >= 0 && A->n <= split_threshold(&s->P)) {
         merge_node(s, a);
         break;
       }
     }
   }
-  /* split the new leaves while they hold more than C charges */
+  /* split the new leaves while they hold more charges than the split threshold */
   for (int t = 0; t < m.n_excl; ++t) {
     int64_t j = m.excl[t];
     int leaf = -1;
@@ -965,7 +970,7 @@ static int check_rec(const or_sys* s, int a, int64_t* seen) {
     if ((s->key[j] >> (3 * (s->P.Dmax - A->depth))) != A->key) return 5;
   }
   if (A->child >= 0) {
-    if (!(A->n > s->P.C && A->depth < s->P.Dmax)) return 6;
+    if (!(A->n > split_threshold(&s->P) && A->depth < s->P.Dmax)) return 6;
     int64_t sum = 0;
     for (int o = 0; o < 8; ++o) {
       const or_node* Ch = &s->nodes[A->child + o];
@@ -976,7 +981,7 @@ static int check_rec(const or_sys* s, int a, int64_t* seen) {
     }
     if (sum != A->n) return 8;
   } else {
-    if (!(A->n <= s->P.C)) return 9; /* also at depth Dmax (capacity rule) */
+    if (!(A->n <= (A->depth < s->P.Dmax ? split_threshold(&s->P) : s->P.C))) return 9; /* capacity rule at Dmax */
     for (int64_t k = 0; k < A->n; ++k) {
       int64_t j = A->idx[k];
       if (seen[j]) return 10;

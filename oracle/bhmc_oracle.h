@@ -47,7 +47,8 @@ typedef struct {
   double theta;     /* opening parameter of the MAC rho_A / r_{i,A} <= theta, Sec. 3.2 */
   int32_t p;        /* truncation order of the Taylor expansion, Eq. (3.3) */
   int32_t N0;       /* minimum expansion number N_0, Sec. 3.2 */
-  int32_t C;        /* leaf capacity: a node splits when it holds more than C charges */
+  int32_t C;        /* leaf capacity: a node splits when it holds more than C charges
+                       (more than 0 with fixed_depth); no depth-Dmax leaf holds more */
   int32_t Dmax;     /* deepest level */
   double root_lo[3];/* lower corner of the root cube (Sec. 3.2 root cluster) */
   double root_side; /* side of the root cube, a power of two */
@@ -57,6 +58,8 @@ typedef struct {
   double image_R;   /* image position R^2 r / |r|^2 */
   double image_alpha; /* image charge alpha * q * R / |r| */
   double hard_core; /* common diameter tau of the mobile ions (Eq. 2.1), 0: none */
+  int32_t fixed_depth; /* 1: the Sec. 3.2 tree of fixed level L_max = Dmax: every
+                          non-empty cluster above Dmax splits, leaves are at Dmax */
 } or_params;
 
 typedef struct or_sys or_sys;

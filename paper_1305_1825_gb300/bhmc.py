@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("shell", C.c_int32), ("shell_rmin", C.c_double), ("shell_rmax", C.c_double),
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
         ("precision", C.c_int32), ("warps", C.c_int32), ("layout", C.c_int32),
-        ("node_factor", C.c_double), ("hard_core", C.c_double),
+        ("node_factor", C.c_double), ("hard_core", C.c_double), ("fixed_depth", C.c_int32),
     ]
 
 
@@ -151,6 +151,7 @@ def make_params(d: dict, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_fa
     P.layout = d.get("layout", layout)
     P.node_factor = d.get("node_factor", node_factor)
     P.hard_core = d.get("hard_core", 0.0) or 0.0
+    P.fixed_depth = 1 if d.get("fixed_depth", False) else 0
     return P
 
 
@@ -305,12 +306,17 @@ def bhmc_export_tree(h, K=None):
     """{(depth, key): (is_leaf, count, members or None)} and, if K is given, moments per key."""
     n = bhmc_n_charges(h)
     cap = 8 * n + 1024
-    rows = np.zeros((cap, 4), dtype=np.int64)
     mem = np.zeros(n + 8, dtype=np.int64)
-    M = np.zeros((cap, K)) if K else None
     nr = C.c_int64()
-    _check(lib().bhmc_export_tree(h, rows.ctypes.data_as(_i64p), cap, mem.ctypes.data_as(_i64p), len(mem),
-                                  M.ctypes.data_as(_dp) if K else None, C.byref(nr)), "bhmc_export_tree")
+    for attempt in range(4):  # deep (fixed-level) trees hold more clusters than charges
+        rows = np.zeros((cap, 4), dtype=np.int64)
+        M = np.zeros((cap, K)) if K else None
+        rc = lib().bhmc_export_tree(h, rows.ctypes.data_as(_i64p), cap, mem.ctypes.data_as(_i64p), len(mem),
+                                    M.ctypes.data_as(_dp) if K else None, C.byref(nr))
+        if rc != EINVAL or attempt == 3:
+            break
+        cap *= 8
+    _check(rc, "bhmc_export_tree")
     tree, moms = {}, {}
     off = 0
     for r in range(nr.value):

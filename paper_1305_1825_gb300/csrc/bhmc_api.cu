@@ -92,6 +92,7 @@ static bhmc_status validate(const bhmc_params* P) {
   if (!(P->lB > 0.0) || !(P->beta >= 0.0) || !(P->theta >= 0.0 && P->theta < 1.0)) return BHMC_EINVAL;
   if (P->p < 0 || P->p > BHMC_MAX_P) return BHMC_EINVAL;
   if (P->N0 < 0 || P->C < 2 || P->C > BHMC_MAX_C || P->Dmax < 1 || P->Dmax > BHMC_MAX_D) return BHMC_EINVAL;
+  if (P->fixed_depth != 0 && P->fixed_depth != 1) return BHMC_EINVAL;
   if (!pow2(P->root_side)) return BHMC_EINVAL;
   const double hmin = std::ldexp(P->root_side, -P->Dmax);
   for (int a = 0; a < 3; ++a) {
@@ -263,6 +264,7 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.Kp = pad4(S.K);
   S.N0 = P->N0;
   S.C = P->C;
+  S.Cs = P->fixed_depth ? 0 : P->C;
   S.Dmax = P->Dmax;
   S.images = P->images ? 1 : 0;
   S.shell = P->shell ? 1 : 0;
@@ -289,7 +291,12 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.hc2 = P->hard_core * P->hard_core;
   S.hc2f = (float)S.hc2;
   S.img_alpha = P->image_alpha;
-  const double f = P->node_factor > 0.0 ? P->node_factor : (1.0 + std::max(1.0, 8.0 / P->C));
+  double f = 1.0 + std::max(1.0, 8.0 / P->C);
+  if (P->fixed_depth) {  // a chain of clusters down to Dmax above every charge
+    const int l8 = (int)std::floor(std::log((double)std::max<long long>(S.n_tot, 1)) / std::log(8.0));
+    f = 8.0 * (double)std::max(1, P->Dmax - l8 + 1);
+  }
+  if (P->node_factor > 0.0) f = P->node_factor;
   long long cap = 64 + (long long)std::ceil(f * (double)S.n_tot);
   cap = (cap + 7) & ~7LL;
   S.node_cap = (int)std::min<long long>(cap, (1LL << 28));
@@ -383,7 +390,7 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
     cleanup();
     return rc;
   }
-  int n_list = (S.n_tot > S.C && S.Dmax > 0) ? 1 : 0;
+  int n_list = (S.n_tot > S.Cs && S.Dmax > 0) ? 1 : 0;
   int zero = 0;
   if (cudaMemcpyAsync(la, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cleanup();

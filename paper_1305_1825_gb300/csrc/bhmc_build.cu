@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_split_level(SysDev S, const int* list, 
                                (o & 4) ? a.z + hc : a.z - hc, hc);
     S.nB[c0 + o] = make_int4(-1, counts[o], (int)(unsigned)(ck & 0xffffffffULL), (int)(unsigned)(ck >> 32));
     seg[c0 + o] = st + start[o];
-    next_flags[8 * blockIdx.x + o] = (counts[o] > S.C && depth + 1 < S.Dmax) ? c0 + o : -1;
+    next_flags[8 * blockIdx.x + o] = (counts[o] > S.Cs && depth + 1 < S.Dmax) ? c0 + o : -1;
   }
   if (threadIdx.x == 0) S.nB[node].x = c0;
 }

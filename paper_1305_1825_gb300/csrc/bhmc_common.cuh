@@ -34,6 +34,7 @@ __host__ __device__ constexpr int tidx(int n1, int n2, int n3) {
 struct SysDev {
   int n_mob, n_fix, n_tot;
   int p, K, Kp, N0, C, Dmax;
+  int Cs;                   // split threshold: C, or 0 for the fixed-level tree
   int images, shell, prec, layout;
   double lB, beta, theta2;
   float theta2f, lBf;

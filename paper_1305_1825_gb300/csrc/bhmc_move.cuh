@@ -491,44 +491,82 @@ __device__ __forceinline__ void team_sync(int bar, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
 }
 
-// Local adjustment (Sec. 3.3) of an accepted move.  Requires complete paths
-// and leaf counts (complete_paths).  The first nt threads of the block (all
-// when nt == 0) run it, synchronised by barrier `bar` (0: __syncthreads).
-static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt = 0, int bar = 0) {
+// (A0) of the local adjustment (Sec. 3.3): q (r - r_A)^k, (r - r_A)^k along
+// the old and new paths of both moved charges in FP64, one thread per
+// (charge, side, level) with the three axes' powers built by repeated
+// multiplication (the charge folded into the x powers), and the pre-move leaf
+// slots.  Threads t0 .. t0 + n - 1 run it; it reads only the move's setup and
+// its complete paths, so it may run before the Metropolis decision.
+static __device__ void commit_prep(const SysDev& S, MoveStore& st, int t0, int n) {
   MoveSh& sh = st.sh;
-  const int K = S.K, SC = S.C + 2, P = S.p;
-  const int tid = threadIdx.x, nth = nt > 0 ? nt : (int)blockDim.x;
+  const int P = S.p;
   constexpr int NL = BHMC_MAX_D + 1;
-  // (A0) powers (r - r_A)^k along both paths of both moved charges (FP64,
-  // built by repeated multiplication as in the definition of the moments)
-  for (int it = tid; it < sh.nmov * 2 * NL * 3; it += nth) {
-    const int ax = it % 3;
-    int r = it / 3;
-    const int d = r % NL;
-    r /= NL;
-    const int side = r & 1, m = r >> 1;
-    const int ps = 2 * m + side;
+  const int tid = (int)threadIdx.x - t0;
+  if (tid < 0 || tid >= n) return;
+  for (int it = tid; it < sh.nmov * 2 * NL; it += n) {
+    const int ps = it / NL, d = it - ps * NL;
     if (d > sh.plen[ps]) continue;
+    const int m = ps >> 1, side = ps & 1;
     const float4 c = S.nA[sh.path[ps][d]];
     const double* X = m ? (side ? sh.bi : sh.ai) : (side ? sh.b : sh.a);
-    const double diff = __dsub_rn(X[ax], (double)(ax == 0 ? c.x : (ax == 1 ? c.y : c.z)));
-    double* pw = st.pw[m][side][d][ax];
-    double v = 1.0;
-    pw[0] = v;
+    const double q = m ? (side ? sh.qb_img : sh.qa_img) : sh.q;
+    const double dx = __dsub_rn(X[0], (double)c.x), dy = __dsub_rn(X[1], (double)c.y),
+                 dz = __dsub_rn(X[2], (double)c.z);
+    double* px = st.pw[m][side][d][0];
+    double* py = st.pw[m][side][d][1];
+    double* pz = st.pw[m][side][d][2];
+    double vx = q, vy = 1.0, vz = 1.0;
+    px[0] = vx;
+    py[0] = vy;
+    pz[0] = vz;
     for (int k = 1; k <= P; ++k) {
-      v = __dmul_rn(v, diff);
-      pw[k] = v;
+      vx = __dmul_rn(vx, dx);
+      vy = __dmul_rn(vy, dy);
+      vz = __dmul_rn(vz, dz);
+      px[k] = vx;
+      py[k] = vy;
+      pz[k] = vz;
     }
   }
-  if (tid == 0) sh.slot_i = S.slot_of[sh.i];
-  if (tid == 1 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
+  if (tid == n - 1) sh.slot_i = S.slot_of[sh.i];
+  if (tid == n - 2 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
   if (tid < 2) sh.merge_d[tid] = 1 << 20;
-  team_sync(bar, nth);
-  // (A1) FP64 moments per level, both moved charges in one pass: for each
-  // (level, term) the ion's update, then the image's (their paths share
-  // clusters, and a cluster belongs to one level, so one thread owns each
-  // (cluster, term)); same cluster -> M += mb - ma, else M_old -= ma and
-  // M_new += mb.  The last thread moves the leaf slots meanwhile.
+}
+
+// Index of the first of the four path clusters (old/new of the ion, old/new
+// of the image) that holds the same cluster as a[k] (k itself when none before it does).
+__device__ __forceinline__ int first_of(const int a[4], int k) {
+  for (int j = 0; j < k; ++j)
+    if (a[j] == a[k]) return j;
+  return k;
+}
+
+// v[k] and v[k] = x for a run-time k in 0..3 without indexing the array
+// (selects keep it in registers).
+__device__ __forceinline__ double pick4(const double v[4], int k) {
+  return k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
+}
+__device__ __forceinline__ void put4(double v[4], int k, double x) {
+  v[0] = k == 0 ? x : v[0];
+  v[1] = k == 1 ? x : v[1];
+  v[2] = k == 2 ? x : v[2];
+  v[3] = k == 3 ? x : v[3];
+}
+
+// Local adjustment (Sec. 3.3) of an accepted move after commit_prep.  The
+// first nt threads of the block (all when nt == 0) run it, synchronised by
+// barrier `bar` (0: __syncthreads).
+static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int bar) {
+  MoveSh& sh = st.sh;
+  const int K = S.K, SC = S.C + 2;
+  const int tid = threadIdx.x, nth = nt > 0 ? nt : (int)blockDim.x;
+  constexpr int NL = BHMC_MAX_D + 1;
+  // (A1) FP64 moments per level, both moved charges in one pass: one thread
+  // owns each (level, term), the four path clusters of that level (a cluster
+  // belongs to one level) are read together, then the ion's update and the
+  // image's are applied in that order (same cluster -> M += mb - ma, else
+  // M_old -= ma and M_new += mb) and each distinct cluster written once.  The
+  // last thread moves the leaf slots meanwhile.
   {
     int Dn = 0;
     for (int ps = 0; ps < 2 * sh.nmov; ++ps) Dn = max(Dn, sh.plen[ps] + 1);
@@ -537,35 +575,38 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
     for (int it = tid; tid < nw && it < Dn * K; it += nw) {
       const int d = it / K, t = it - d * K;
       const int n1 = sh.ex[t][0], n2 = sh.ex[t][1], n3 = sh.ex[t][2];
-      for (int m = 0; m < sh.nmov; ++m) {
-        const int pa = 2 * m, pb = 2 * m + 1;
-        const int na = d <= sh.plen[pa] ? sh.path[pa][d] : -1;
-        const int nb = d <= sh.plen[pb] ? sh.path[pb][d] : -1;
-        const double qa = m ? sh.qa_img : sh.q, qb = m ? sh.qb_img : sh.q;
-        double ma = 0.0, mb = 0.0;
-        if (na >= 0)
-          ma = __dmul_rn(qa, __dmul_rn(__dmul_rn(st.pw[m][0][d][0][n1], st.pw[m][0][d][1][n2]),
-                                       st.pw[m][0][d][2][n3]));
-        if (nb >= 0)
-          mb = __dmul_rn(qb, __dmul_rn(__dmul_rn(st.pw[m][1][d][0][n1], st.pw[m][1][d][1][n2]),
-                                       st.pw[m][1][d][2][n3]));
-        if (na >= 0 && na == nb) {
-          double* M = &S.M64[(size_t)na * K + t];
-          *M = __dadd_rn(*M, __dsub_rn(mb, ma));
-          mirror(S, na, t, *M);
-        } else {
-          if (na >= 0) {
-            double* M = &S.M64[(size_t)na * K + t];
-            *M = __dsub_rn(*M, ma);
-            mirror(S, na, t, *M);
-          }
-          if (nb >= 0) {
-            double* M = &S.M64[(size_t)nb * K + t];
-            *M = __dadd_rn(*M, mb);
-            mirror(S, nb, t, *M);
-          }
-        }
+      int a[4];
+      double v[4], mab[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = (k < 2 * sh.nmov && d <= sh.plen[k]) ? sh.path[k][d] : -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = a[k] >= 0 ? S.M64[(size_t)a[k] * K + t] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int m = k >> 1, side = k & 1;
+        mab[k] = a[k] >= 0 ? __dmul_rn(__dmul_rn(st.pw[m][side][d][0][n1], st.pw[m][side][d][1][n2]),
+                                       st.pw[m][side][d][2][n3])
+                           : 0.0;
       }
+      int own[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) own[k] = first_of(a, k);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int ka = 2 * m, kb = 2 * m + 1;
+        const bool same = a[ka] >= 0 && a[ka] == a[kb];
+        if (a[ka] >= 0) {  // old cluster: M -= ma, or M += mb - ma when it is also the new one
+          const double x = pick4(v, own[ka]);
+          put4(v, own[ka], same ? __dadd_rn(x, __dsub_rn(mab[kb], mab[ka])) : __dsub_rn(x, mab[ka]));
+        }
+        if (a[kb] >= 0 && !same) put4(v, own[kb], __dadd_rn(pick4(v, own[kb]), mab[kb]));
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (a[k] >= 0 && own[k] == k) {
+          S.M64[(size_t)a[k] * K + t] = v[k];
+          mirror(S, a[k], t, v[k]);
+        }
     }
     for (int it = tid; it < sh.nmov * NL; it += nth) {
       const int mm = it / NL, d = it - mm * NL;
@@ -579,12 +620,13 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
     }
     team_sync(bar, nth);
   }
-  // (C) merge the topmost internal cluster on an old path holding <= C charges
+  // (C) merge the topmost internal cluster on an old path holding no more
+  // charges than the split threshold
   for (int it = tid; it < sh.nmov * NL; it += nth) {
     const int m = it / NL, d = it - m * NL;
     if (d > sh.plen[2 * m]) continue;
     const int4 b = S.nB[sh.path[2 * m][d]];
-    if (b.x >= 0 && b.y <= S.C) atomicMin(&sh.merge_d[m], d);
+    if (b.x >= 0 && b.y <= S.Cs) atomicMin(&sh.merge_d[m], d);
   }
   team_sync(bar, nth);
   if (tid == 0) {
@@ -597,7 +639,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
     }
   }
   team_sync(bar, nth);
-  // (D) split the new leaves while they hold more than C charges.  Without a
+  // (D) split the new leaves while they hold more charges than the split threshold.  Without a
   // merge the new leaves' counts follow from the pre-move counts.
   bool may_split = true;
   if (sh.merge_d[0] >= NL && (sh.nmov < 2 || sh.merge_d[1] >= NL)) {
@@ -609,7 +651,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
         const int ua = sh.path[2 * u][sh.plen[2 * u]], ub = sh.path[2 * u + 1][sh.plen[2 * u + 1]];
         if (ua != ub) c += (ub == L) - (ua == L);
       }
-      if (c > S.C) may_split = true;
+      if (c > S.Cs) may_split = true;
     }
   }
   for (int m = 0; m < sh.nmov && may_split; ++m) {
@@ -621,7 +663,7 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
         const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
         const int dL = key_depth(key);
         sh.split_node = -1;
-        if (b.y > S.C && dL < S.Dmax) {
+        if (b.y > S.Cs && dL < S.Dmax) {
           const int g = alloc_group(S);
           if (g < 0) {
             set_err(S, BHMC_ENOMEM_POOL);
@@ -674,6 +716,16 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
       team_sync(bar, nth);
     }
   }
+}
+
+// Local adjustment (Sec. 3.3) of an accepted move.  Requires complete paths
+// and leaf counts (complete_paths).  The first nt threads of the block (all
+// when nt == 0) run it, synchronised by barrier `bar` (0: __syncthreads).
+static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt = 0, int bar = 0) {
+  const int nth = nt > 0 ? nt : (int)blockDim.x;
+  commit_prep(S, st, 0, nth);
+  team_sync(bar, nth);
+  commit_apply(S, st, nt, bar);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,6 +800,8 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
       if (threadIdx.x == 160) sh.nxt_m = m + 1;
     } else {
       const int nt = ahead ? 160 : (int)blockDim.x, bar = ahead ? 2 : 0;
+      // warp 0 decides while the other warps of the team prepare the commit
+      const bool early = nt > 32;
       complete_paths(S, sh);
       team_sync(bar, nt);
       if (threadIdx.x == 0 && sh.outcome < 0) {
@@ -761,9 +815,14 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
         else
           sh.outcome = BHMC_ACCEPT;
       }
+      if (early) commit_prep(S, st, 32, nt - 32);
       team_sync(bar, nt);
       if (sh.outcome == BHMC_ACCEPT) {
-        commit_move_block(S, st, nt, bar);
+        if (!early) {
+          commit_prep(S, st, 0, nt);
+          team_sync(bar, nt);
+        }
+        commit_apply(S, st, nt, bar);
         if (threadIdx.x == 0) *S.energy += sh.dE;
       }
     }

@@ -138,13 +138,16 @@ def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8)
                 step=1.0, seed=seed)
 
 
-def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int = 8) -> dict:
+def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int = 8,
+             Lmax: int = 0) -> dict:
     """The electric double layer of Sec. 4 with its hard cores (Eq. 2.1): n
     counterions of valence 2 and diameter 4 around a fixed macroion of radius
     30 and valence -2n in a cell of radius 80, l_B = 7.14.  Ion centres lie in
     [32, 78] (contact with the macroion and the cell wall), placed one by one
     uniformly in that shell, each redrawn until it is farther than 4 from all
-    ions placed before (random sequential addition)."""
+    ions placed before (random sequential addition).  Lmax > 0 selects the
+    fixed-level tree of Sec. 3.2 with leaves at depth Lmax (root cube of side
+    256: Lmax = 6 gives leaves of side tau, which hold at most 4 ions)."""
     rng = np.random.default_rng(seed)
     a, rcell, tau = 30.0, 80.0, 4.0
     rmin, rmax = a + tau / 2, rcell - tau / 2
@@ -164,9 +167,11 @@ def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int
     lo, side = root_for(rcell)
     params = base_params(lB=7.14, theta=theta, p=p, C=C, root_lo=lo, root_side=side,
                          shell=(rmin, rmax), hard_core=tau)
+    if Lmax > 0:
+        params.update(Dmax=Lmax, fixed_depth=True)
     q = np.concatenate([np.full(n, 2.0), [-2.0 * n]])
     xyz = np.concatenate([xyz, np.zeros((1, 3))], axis=0)
-    return dict(name="edl-hard-N%d" % n, params=params, q=q, xyz=xyz, n_mobile=n, n_fixed=1,
+    return dict(name="edl-hard-N%d%s" % (n, "-L%d" % Lmax if Lmax > 0 else ""), params=params, q=q, xyz=xyz, n_mobile=n, n_fixed=1,
                 step=2.0, seed=seed)
 
 

@@ -220,6 +220,29 @@ def test_tree_matches_brute_force_including_ties(oracle_mod):
         assert s.export_tree() == brute_tree(xyz, params["root_lo"], params["root_side"], C, Dmax)
 
 
+def test_fixed_depth_tree_matches_brute_force(oracle_mod):
+    """The Sec. 3.2 tree of fixed level L_max: every non-empty cluster above L_max
+    is bisected, so every charge sits in a leaf at depth L_max (the brute-force
+    tree with split threshold 0), and the leaf counts reproduce a histogram of
+    the points over the 8^L_max cells."""
+    rng = np.random.default_rng(23)
+    for Lmax in (3, 4, 5):
+        xyz = np.round(rng.uniform(-8, 8, (300, 3)) * 2) / 2
+        xyz = np.unique(xyz, axis=0)[:250]
+        params = W.base_params(C=32, Dmax=Lmax)
+        params["fixed_depth"] = True
+        s = oracle_mod.System(params, np.ones(len(xyz)), xyz, n_mobile=len(xyz))
+        assert s.check() == 0
+        tree = s.export_tree()
+        assert tree == brute_tree(xyz, params["root_lo"], params["root_side"], 0, Lmax)
+        lo, side = np.array(params["root_lo"]), params["root_side"]
+        cell = np.floor((xyz - lo) / (side / 2 ** Lmax)).astype(int)
+        _, hist = np.unique(cell, axis=0, return_counts=True)
+        leaves = sorted(c for (d, k), (leaf, c, _) in tree.items() if leaf and c > 0)
+        assert all(d == Lmax for (d, k), (leaf, c, _) in tree.items() if leaf and c > 0)
+        assert leaves == sorted(hist.tolist())
+
+
 def test_capacity_rule_at_dmax(oracle_mod):
     params = W.base_params(C=2, Dmax=3)
     xyz = np.array([[0.1, 0.1, 0.1], [0.2, 0.2, 0.2], [0.3, 0.1, 0.2], [5.0, 5.0, 5.0]])
@@ -237,7 +260,7 @@ def _rebuilt(oracle_mod, s, wl):
     return oracle_mod.System(wl["params"], q[:n], x[:n], s.n_mobile, s.n_fixed)
 
 
-@pytest.mark.parametrize("kind", ["plain", "colloid"])
+@pytest.mark.parametrize("kind", ["plain", "colloid", "fixed-depth"])
 def test_commit_equals_rebuild(oracle_mod, kind):
     """After every local adjustment (with splits and merges) the tree equals the
     tree built from scratch from the new particle set, and the running moments
@@ -246,9 +269,12 @@ def test_commit_equals_rebuild(oracle_mod, kind):
     if kind == "plain":
         wl = W.plain(n=300, seed=8, C=2)
         wl["params"]["Dmax"] = 9
-    else:
+    elif kind == "colloid":
         wl = W.colloid(n=200, seed=9, C=3)
         wl["params"]["Dmax"] = 10
+    else:  # the fixed-level tree of Sec. 3.2: merges and splits reach down to Dmax
+        wl = W.plain(n=300, seed=8, C=4)
+        wl["params"].update(Dmax=5, fixed_depth=True)
     s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
     done = 0
     for t in range(400):
