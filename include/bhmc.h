@@ -61,7 +61,9 @@ typedef struct {
   double lB;          /* Bjerrum length (> 0) */
   double beta;        /* inverse temperature of the Metropolis rule (>= 0) */
   double theta;       /* MAC: multipole iff rho_A/|r_A - x| <= theta, 0 <= theta < 1 */
-  int32_t p;          /* Taylor truncation order, 0..6 (the oracle goes to 10) */
+  int32_t p;          /* Taylor truncation order, 0..10.  With FP32 traversal the order-p terms
+                         T_n overflow for accepted clusters closer than about 2e-3 length
+                         units at p = 10 (1e-5 at p = 6); BHMC_PREC_F64 has no such limit */
   int32_t N0;         /* minimum expansion number (>= 0) */
   int32_t C;          /* leaf capacity, 2..32: a cluster holding more than C charges splits (more
                          than 0 with fixed_depth); no depth-Dmax cell may hold more than C */

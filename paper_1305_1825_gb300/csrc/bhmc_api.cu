@@ -184,7 +184,7 @@ static WMap wmap_make(int p) {
 }
 static int wmap_nnz(int p) { return (int)wmap_make(p).col.size(); }
 
-// Calls f(std::integral_constant<int, p>{}) for the multipole order p (0..6).
+// Calls f(std::integral_constant<int, p>{}) for the multipole order p (0..10).
 template <typename F>
 static auto by_p(int p, F&& f) {
   switch (p) {
@@ -194,7 +194,11 @@ static auto by_p(int p, F&& f) {
     case 3: return f(std::integral_constant<int, 3>{});
     case 4: return f(std::integral_constant<int, 4>{});
     case 5: return f(std::integral_constant<int, 5>{});
-    default: return f(std::integral_constant<int, 6>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 7: return f(std::integral_constant<int, 7>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    default: return f(std::integral_constant<int, 10>{});
   }
 }
 
@@ -748,7 +752,7 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   }
   std::vector<double> h((size_t)grid * warps);
   int herr = 0;
-  // the FP32 pass at p = 6 evaluates from W32, refreshed here after moves
+  // the FP32 pass at p >= 6 evaluates from W32, refreshed here after moves
   const bool wform = ctx->S.prec == BHMC_PREC_F32 && ctx->S.p >= 6;
   bool ok = (!wform || !ctx->w_stale || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
             cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&

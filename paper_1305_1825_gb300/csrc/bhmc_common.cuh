@@ -7,7 +7,7 @@
 
 #include "../../include/bhmc.h"
 
-#define BHMC_MAX_P 6
+#define BHMC_MAX_P 10
 #define BHMC_MAX_D 20
 #ifndef BHMC_MAX_WARPS
 #define BHMC_MAX_WARPS 8

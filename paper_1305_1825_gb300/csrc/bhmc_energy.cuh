@@ -72,7 +72,7 @@ __device__ __forceinline__ Real lane_multipole(const SysDev& S, const float4& a,
     return (Real)v;
   }
   if (sizeof(Real) == 4) {
-    // p = 6: evaluation coefficients (a third of the recurrence's instructions)
+    // p >= 6: evaluation coefficients (a third of the recurrence's instructions)
     const float rx = (a.x - hi[0]) - lo[0], ry = (a.y - hi[1]) - lo[1], rz = (a.z - hi[2]) - lo[2];
     // the target's own charge, if it lies in the cluster, is removed through its expansion
     const float qe[1] = {(float)q};

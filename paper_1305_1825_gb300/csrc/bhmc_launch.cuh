@@ -62,5 +62,9 @@ BHMC_EXTERN_P(3)
 BHMC_EXTERN_P(4)
 BHMC_EXTERN_P(5)
 BHMC_EXTERN_P(6)
+BHMC_EXTERN_P(7)
+BHMC_EXTERN_P(8)
+BHMC_EXTERN_P(9)
+BHMC_EXTERN_P(10)
 
 }  // namespace bhmc
