@@ -487,7 +487,8 @@ def _field_item(bh, name, wl, reps=3):
 
 def _eq4_1(bh, wl, warps):
     """Eq. (4.1) relative error of the FP32 treecode against the exact sum (theta = 0,
-    FP64): V_i = q_i phi_i over every charge, and over the mobile ions alone."""
+    FP64): V_i = q_i phi_i over every charge, over the mobile ions alone, and of the
+    FP64 treecode over every charge (the truncation error without FP32 rounding)."""
     import numpy as np
     n, nt = wl["n_mobile"], wl["n_mobile"] + wl["n_fixed"]
     ex = bh.Context(dict(wl, params=dict(wl["params"], theta=0.0)), precision=bh.PREC_F64, warps=8)
@@ -496,8 +497,11 @@ def _eq4_1(bh, wl, warps):
     tr = bh.Context(wl, warps=warps, layout=bh.LAYOUT_AOS)
     vt = tr.potentials()[:nt] * np.asarray(wl["q"][:nt])
     tr.close()
+    t64 = bh.Context(wl, precision=bh.PREC_F64, warps=8)
+    v64 = t64.potentials()[:nt] * np.asarray(wl["q"][:nt])
+    t64.close()
     rel = lambda a, b: float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a ** 2)))
-    return rel(v, vt), rel(v[:n], vt[:n])
+    return rel(v, vt), rel(v[:n], vt[:n]), rel(v, v64)
 
 
 def run_suite(args):
@@ -572,24 +576,24 @@ def run_suite(args):
     snap = eqb.replica(0).charges()[1][: base["n_mobile"] + base["n_fixed"]].copy()
     eqb.close()
     for theta in (0.5, 0.3):
-        for pp in range(0, 7):
+        for pp in range(0, 11):
             wl = W.edl_hard(n=800, seed=8, theta=theta, p=pp)
             wl["xyz"] = snap
-            E, E_ions = _eq4_1(bh, wl, args.warps)
+            E, E_ions, E64 = _eq4_1(bh, wl, args.warps)
             rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 1000)
             systems = [W.edl_hard(n=800, seed=8000 + r, theta=theta, p=pp) for r in range(152)]
             rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps,
                                        bh.LAYOUT_AOS, 1000)
             del systems
             emit({"suite": "p-sweep-edl-N800", "theta": theta, "p": pp, "E_eq4_1": E,
-                  "E_eq4_1_ions_only": E_ions, "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b})
+                  "E_eq4_1_ions_only": E_ions, "E_eq4_1_f64_traversal": E64, "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b})
     # the minimum expansion number N0 (Sec. 3.2): small clusters summed directly
     for pp in (2, 4):
         for n0 in (0, 4, 8, 16):
             wl = W.edl_hard(n=800, seed=8, theta=0.5, p=pp)
             wl["xyz"] = snap
             wl["params"]["N0"] = n0
-            E, E_ions = _eq4_1(bh, wl, args.warps)
+            E, E_ions, _ = _eq4_1(bh, wl, args.warps)
             systems = []
             for r in range(152):
                 w2 = W.edl_hard(n=800, seed=8000 + r, theta=0.5, p=pp)

@@ -27,7 +27,7 @@ def test_status_strings_and_validation_without_gpu():
     assert bhmc.bhmc_status_string(bhmc.ECAPACITY).startswith("depth-Dmax")
     # invalid parameters are rejected on the host before any CUDA call
     wl = workloads.plain(n=16)
-    for bad in (dict(p=7), dict(C=1), dict(theta=1.0), dict(root_side=30.0), dict(Dmax=21)):
+    for bad in (dict(p=11), dict(C=1), dict(theta=1.0), dict(root_side=30.0), dict(Dmax=21)):
         d = dict(wl["params"], **bad)
         P = bhmc.make_params(d)
         h = ctypes.c_void_p()

@@ -59,7 +59,7 @@ def test_build_matches_oracle(bh, oracle_mod, kind):
 
 
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
-@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_delta_energy_matches_oracle(bh, oracle_mod, theta, p):
     wl = W.colloid(n=2000, seed=5, theta=theta, p=p)
     ref = _oracle(oracle_mod, wl)
@@ -77,6 +77,25 @@ def test_delta_energy_matches_oracle(bh, oracle_mod, theta, p):
             assert abs(dE - e.dE) <= REL * abs(e.dE) + FLOOR32 * e.abs_sum, (dE, e.dE, e.abs_sum)
         assert n > 20
         ctx.close()
+
+
+@pytest.mark.parametrize("p", [8, 10])
+def test_delta_energy_high_order_f64(bh, oracle_mod, p):
+    """All-FP64 traversal at the highest orders against the oracle."""
+    wl = W.colloid(n=1500, seed=15, p=p)
+    ref = _oracle(oracle_mod, wl)
+    ctx = bh.Context(wl, precision=bh.PREC_F64, warps=4)
+    n = 0
+    for i, b in _moves(wl, 40, seed=70 + p):
+        rc, dE, cnt = ctx.delta_energy(i, b)
+        e = ref.delta_energy(i, b)
+        assert rc == e.status
+        if rc:
+            continue
+        n += 1
+        assert (cnt.visited, cnt.accepted, cnt.pairs) == (e.visited, e.accepted, e.pairs)
+        assert abs(dE - e.dE) <= FLOOR64 * e.abs_sum
+    assert n > 20
 
 
 def test_delta_energy_plain_config_every_move(bh, oracle_mod):
@@ -236,7 +255,7 @@ def test_energy_counters_match_oracle(bh, oracle_mod, precision):
 
 
 @pytest.mark.parametrize("layout", [0, 1])
-@pytest.mark.parametrize("p", [4, 6])
+@pytest.mark.parametrize("p", [4, 6, 10])
 def test_energy_after_chain(bh, oracle_mod, layout, p):
     """The full-energy pass after a chain of accepted moves (at p = 6 it
     evaluates coefficients refreshed from the running moments) against the
@@ -254,10 +273,10 @@ def test_energy_after_chain(bh, oracle_mod, layout, p):
     assert abs(e_tree - e_ref) <= 2e-6 * abs(e_ref) + 2e-6 * scale
 
 
-@pytest.mark.parametrize("p", [2, 6])
+@pytest.mark.parametrize("p", [2, 6, 10])
 def test_potentials_sampled(bh, oracle_mod, p):
     """Per-charge treecode potentials of the full-energy pass (recurrence at
-    p = 2, evaluation coefficients at p = 6) against the oracle, sampled."""
+    p = 2, evaluation coefficients at p = 6 and 10) against the oracle, sampled."""
     wl = W.colloid(n=2000, seed=14, p=p)
     ctx = bh.Context(wl, warps=4, layout=1)
     ref = _oracle(oracle_mod, wl)
@@ -269,7 +288,7 @@ def test_potentials_sampled(bh, oracle_mod, p):
         assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
 
 
-@pytest.mark.parametrize("p", [0, 1, 3, 5])
+@pytest.mark.parametrize("p", [0, 1, 3, 5, 7, 8, 9, 10])
 def test_chain_and_energy_every_order(bh, oracle_mod, p):
     """Orders beyond the benchmark's: a batched chain (8 warps) and the full
     energy against the oracle."""
