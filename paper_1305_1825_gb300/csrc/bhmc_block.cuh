@@ -247,6 +247,10 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         }
         if (LAYOUT == BHMC_LAYOUT_AOS && mac)
           prefetch_range(S.M32 + (size_t)node * pad4(nterms(P)), pad4(nterms(P)) * 4);
+        if ((open | fdc) && fc >= 0) {  // the children's headers, popped next round
+          prefetch_l1(S.nA + fc);
+          prefetch_l1(S.nB + fc);
+        }
         if (dir || ovd) {
           prefetch_range(S.sA + (size_t)node * SC, cnt * 16);
           prefetch_range(S.sB + (size_t)node * SC, cnt * 16);
