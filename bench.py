@@ -418,6 +418,20 @@ def _plain_moves(bh, wl, warps, layout, moves, precision=0):
     return moves / (ms / 1e3)
 
 
+def _spec_moves(bh, wl, warps, layout, moves, proposals):
+    """One chain in one launch of a cluster of `proposals` CTAs (speculative trials)."""
+    import torch
+    ctx = bh.Context(wl, warps=warps, layout=layout)
+    step = wl.get("step", 1.0)
+    ctx.step_mc_spec(200, step, seed=wl.get("seed", 1), move0=0, proposals=proposals)
+    ms, out = _ev_time(lambda: ctx.step_mc_spec(moves, step, seed=wl.get("seed", 1), move0=200,
+                                                proposals=proposals))
+    acc = out[0].accepted / max(out[0].moves, 1)
+    ctx.close()
+    torch.cuda.synchronize()
+    return moves / (ms / 1e3), acc
+
+
 def _batched_moves(bh, systems, seeds, warps, layout, moves):
     b = bh.Batch(systems, warps=warps, layout=layout)
     step = systems[0].get("step", 1.0)
@@ -562,6 +576,17 @@ def run_suite(args):
                   "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
                   "acceptance": acc,
                   "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
+
+    # one chain (the paper's setting): one launch per trial move against one
+    # persistent launch of a cluster of K CTAs that evaluates K trials at once
+    for wl in (W.edl_hard(n=800, seed=8), W.edl_hard(n=10000, seed=8), W.colloid(n=10000, seed=2, C=args.C)):
+        line = {"suite": "single-chain-" + wl["name"], "theta": wl["params"]["theta"], "p": wl["params"]["p"],
+                "gpu_plain_moves_per_s": _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 1000)}
+        for k in (1, 2, 4, 8):
+            rate, acc = _spec_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 20000, k)
+            line["gpu_cluster_%d_proposals_moves_per_s" % k] = rate
+            line["acceptance"] = acc
+        emit(line)
 
     # error and speed against the multipole order (the paper's Figs. 5 and 7):
     # Eq. (4.1) E = sqrt(sum_i |V_i - Vt_i|^2 / sum_i |V_i|^2) over the ions,

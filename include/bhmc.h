@@ -157,6 +157,19 @@ bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]);
 bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed,
                          uint64_t move0, bhmc_mc_stats* stats, bhmc_move_record* records);
 
+/* The same chain as bhmc_step_mc (same trials, outcomes, records and final
+   state), in one launch of a thread-block cluster of `proposals` CTAs
+   (1..BHMC_MAX_PROPOSALS): each step evaluates trials m .. m+proposals-1
+   concurrently against the current tree and keeps them up to the first
+   acceptance, which is committed; a trial evaluated while every earlier trial
+   of its step was rejected sees the tree the sequential chain would see
+   (Sec. 2: a rejected move leaves the configuration unchanged).  Speeds up a
+   single chain by up to 1/acceptance.  EINVAL for proposals outside the range. */
+#define BHMC_MAX_PROPOSALS 8
+bhmc_status bhmc_step_mc_spec(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed,
+                              uint64_t move0, int32_t proposals, bhmc_mc_stats* stats,
+                              bhmc_move_record* records);
+
 /* n_moves Metropolis-adjusted Langevin single-ion trials, one launch each: the
    ion's energy U(x) (the potential of the tree without the ion and its image,
    at the ion and at its image, plus the pair term) and its gradient at the

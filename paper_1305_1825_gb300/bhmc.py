@@ -83,6 +83,8 @@ def lib():
         L.bhmc_commit_move.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                    C.POINTER(McStats), C.c_void_p]
+        L.bhmc_step_mc_spec.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
+                                        C.c_int32, C.POINTER(McStats), C.c_void_p]
         L.bhmc_energy_counters.argtypes = [C.c_void_p, _dp, C.POINTER(Counters)]
         L.bhmc_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
         L.bhmc_batch_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
@@ -204,6 +206,15 @@ def bhmc_step_mc(h, n_moves, step, seed, move0=0, records=False):
     rec = np.zeros(n_moves, dtype=RECORD_DTYPE) if records else None
     rp = C.c_void_p(rec.ctypes.data) if records and n_moves else C.c_void_p(0)
     _check(lib().bhmc_step_mc(h, n_moves, step, seed, move0, C.byref(st), rp), "bhmc_step_mc")
+    return st, rec
+
+
+def bhmc_step_mc_spec(h, n_moves, step, seed, move0=0, proposals=4, records=False):
+    st = McStats()
+    rec = np.zeros(n_moves, dtype=RECORD_DTYPE) if records else None
+    rp = C.c_void_p(rec.ctypes.data) if records and n_moves else C.c_void_p(0)
+    _check(lib().bhmc_step_mc_spec(h, n_moves, step, seed, move0, proposals, C.byref(st), rp),
+           "bhmc_step_mc_spec")
     return st, rec
 
 
@@ -405,6 +416,9 @@ class Context:
 
     def step_mc(self, n_moves, step, seed, move0=0, records=False):
         return bhmc_step_mc(self.h, n_moves, step, seed, move0, records)
+
+    def step_mc_spec(self, n_moves, step, seed, move0=0, proposals=4, records=False):
+        return bhmc_step_mc_spec(self.h, n_moves, step, seed, move0, proposals, records)
 
     def step_mala(self, n_moves, tau, seed, move0=0, records=False):
         return bhmc_step_mala(self.h, n_moves, tau, seed, move0, records)

@@ -624,6 +624,42 @@ bhmc_status bhmc_step_mc(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t 
   return BHMC_OK;
 }
 
+bhmc_status bhmc_step_mc_spec(bhmc_ctx* ctx, uint64_t n_moves, double step, uint64_t seed, uint64_t move0,
+                              int32_t proposals, bhmc_mc_stats* stats, bhmc_move_record* records) {
+  bhmc_status rc = ctx_check(ctx);
+  if (rc != BHMC_OK) return rc;
+  ctx->w_stale = true;
+  if (!stats || !(step >= 0.0) || proposals < 1 || proposals > BHMC_MAX_PROPOSALS) return BHMC_EINVAL;
+  if (n_moves > 0 && ctx->S.n_mob < 1) return BHMC_EINVAL;
+  IoBlock* dio = static_cast<IoBlock*>(ctx->io);
+  IoBlock* hio = static_cast<IoBlock*>(ctx->io_host);
+  MoveRec* drec = nullptr;
+  if (records && n_moves) {
+    if (cudaMalloc(&drec, sizeof(MoveRec) * n_moves) != cudaSuccess) return BHMC_ENOMEM;
+  }
+  CK(cudaMemsetAsync(&dio->stats, 0, sizeof(bhmc_mc_stats), ctx->stream));
+  if (n_moves) {
+    const cudaError_t e = by_p(ctx->P.p, [&](auto PC) {
+      return launch_spec<PC.value>(ctx->S, ctx->P.warps, proposals, move0, n_moves, seed, step, drec,
+                                   &dio->stats, ctx->stream);
+    });
+    if (e != cudaSuccess) {
+      cudaFree(drec);
+      ctx->sticky = BHMC_ECUDA;
+      return BHMC_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(&hio->stats, &dio->stats, sizeof(bhmc_mc_stats), cudaMemcpyDeviceToHost, ctx->stream));
+  if (drec)
+    CK(cudaMemcpyAsync(records, drec, sizeof(MoveRec) * n_moves, cudaMemcpyDeviceToHost, ctx->stream));
+  rc = sync_err(ctx);
+  cudaFree(drec);
+  if (rc != BHMC_OK) return rc;
+  *stats = hio->stats;
+  if (n_moves == 0) bhmc_get_energy(ctx, &stats->energy);
+  return BHMC_OK;
+}
+
 bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t seed, uint64_t move0,
                            bhmc_mc_stats* stats, bhmc_move_record* records) {
   bhmc_status rc = ctx_check(ctx);

@@ -50,6 +50,40 @@ cudaError_t launch_step_mala<BHMC_P>(const SysDev& S, int warps, unsigned long l
   return cudaGetLastError();
 }
 
+template <typename Kern>
+static cudaError_t launch_cluster(Kern kern, int proposals, int warps, cudaStream_t st, const SysDev& S,
+                                  unsigned long long move0, unsigned long long n, uint2 key, double step,
+                                  MoveRec* rec, bhmc_mc_stats* stats) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)proposals, 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * warps), 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)proposals;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, S, move0, n, 0u, key, step, rec, stats);
+}
+
+template <>
+cudaError_t launch_spec<BHMC_P>(const SysDev& S, int warps, int proposals, unsigned long long move0,
+                                unsigned long long n_moves, unsigned long long seed, double step, MoveRec* rec,
+                                bhmc_mc_stats* stats, cudaStream_t st) {
+  const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+  if (S.prec == BHMC_PREC_F64)
+    return launch_cluster(k_spec<BHMC_P, double, BHMC_LAYOUT_SOA>, proposals, warps, st, S, move0, n_moves, key,
+                          step, rec, stats);
+  if (S.layout == BHMC_LAYOUT_AOS)
+    return launch_cluster(k_spec<BHMC_P, float, BHMC_LAYOUT_AOS>, proposals, warps, st, S, move0, n_moves, key,
+                          step, rec, stats);
+  return launch_cluster(k_spec<BHMC_P, float, BHMC_LAYOUT_SOA>, proposals, warps, st, S, move0, n_moves, key, step,
+                        rec, stats);
+}
+
 template <>
 cudaError_t launch_batch<BHMC_P>(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
                                  const BatchArgs* args, int* next, bhmc_mc_stats* stats,

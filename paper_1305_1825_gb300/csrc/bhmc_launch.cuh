@@ -21,6 +21,10 @@ cudaError_t launch_step_mala(const SysDev& S, int warps, unsigned long long m, u
                              unsigned long long seed, double tau, MoveRec* rec, bhmc_mc_stats* stats,
                              cudaStream_t st);
 template <int P>
+cudaError_t launch_spec(const SysDev& S, int warps, int proposals, unsigned long long move0,
+                        unsigned long long n_moves, unsigned long long seed, double step, MoveRec* rec,
+                        bhmc_mc_stats* stats, cudaStream_t st);
+template <int P>
 cudaError_t launch_batch(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
                          const BatchArgs* args, int* next, bhmc_mc_stats* stats, cudaStream_t st);
 template <int P>
@@ -46,6 +50,9 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
   template <> cudaError_t launch_step_mala<P>(const SysDev&, int, unsigned long long, unsigned,              \
                                               unsigned long long, double, MoveRec*, bhmc_mc_stats*,        \
                                               cudaStream_t);                                               \
+  template <> cudaError_t launch_spec<P>(const SysDev&, int, int, unsigned long long,         \
+                                        unsigned long long, unsigned long long, double, MoveRec*,  \
+                                        bhmc_mc_stats*, cudaStream_t);                             \
   template <> cudaError_t launch_batch<P>(const SysDev&, int, const SysDev*, int, int,       \
                                               const BatchArgs*, int*, bhmc_mc_stats*,            \
                                               cudaStream_t);                                     \

@@ -1107,4 +1107,156 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Speculative multi-proposal chain: one thread-block cluster of K CTAs runs a
+// single chain.  In every step CTA r evaluates trial move m + r against the
+// current tree (proposal, rejections, traversal, Metropolis decision,
+// capacity rule); after a cluster barrier every CTA reads the K outcomes from
+// distributed shared memory.  While no earlier move of the step is accepted
+// the tree is the one the sequential chain would see, so the outcomes up to
+// and including the first acceptance j are exactly the sequential chain's:
+// CTA j commits its move, moves m .. m + j are final, and the chain advances
+// by j + 1 (by K when every move was rejected).  The chain, records and
+// statistics equal those of K = 1 and of the plain path.
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// Barrier of every thread of every CTA of the cluster; shared-memory writes
+// before it are visible to the cluster's reads after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// *p in the shared memory of CTA `rank` of this cluster.
+__device__ __forceinline__ int ld_cluster_int(const int* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned ra;
+  int v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// Trial move m up to its decision, the tree unchanged (all threads of the CTA).
+// Returns the outcome, or -1 after a device error (recorded in S.err).
+template <int P, typename Real, int LAYOUT>
+__device__ int spec_eval(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica, uint2 key,
+                         double step) {
+  MoveSh& sh = st.sh;
+  propose(S, sh, m, replica, key, step, 0);
+  __syncthreads();
+  setup_roles(S, sh, 0);
+  __syncthreads();
+  setup_finish(S, sh, 0);
+  __syncthreads();
+  if (sh.outcome < 0) {
+    eval_move<P, Real, LAYOUT>(S, st, true);
+    if (sh.cnt[0][4]) {
+      if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
+      __syncthreads();
+      return -1;
+    }
+    complete_paths(S, sh);
+    __syncthreads();
+    if (threadIdx.x == 0 && sh.outcome < 0) {
+      int acc, fl;
+      metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
+      sh.flagged = fl;
+      if (!acc)
+        sh.outcome = BHMC_REJECT_ENERGY;
+      else if (capacity_violation(S, sh))
+        sh.outcome = BHMC_REJECT_CAPACITY;
+      else
+        sh.outcome = BHMC_ACCEPT;
+    }
+  }
+  __syncthreads();
+  return sh.outcome;
+}
+
+// One chain of n_moves trial moves from move0 on a cluster of K CTAs (see
+// above).  stats must be zeroed by the caller; recs (may be null) receives
+// one record per move.
+template <int P, typename Real, int LAYOUT>
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned long long move0,
+                                                             unsigned long long n_moves, unsigned replica,
+                                                             uint2 key, double step, MoveRec* recs,
+                                                             bhmc_mc_stats* stats) {
+  __shared__ MoveStore st;
+  __shared__ int word;       // this CTA's outcome in the current step (-2: no move, -1: error)
+  __shared__ int plan[3];    // first accepted rank, moves made final, error
+  MoveSh& sh = st.sh;
+  const unsigned rank = cluster_rank(), K = cluster_size();
+  if (*(volatile int*)S.err) return;  // stable during the launch: every CTA returns
+  init_tables(sh, S.K);
+  bhmc_mc_stats loc;
+  loc.moves = loc.accepted = loc.rej_energy = loc.rej_domain = loc.rej_overlap = loc.rej_capacity =
+      loc.flagged = 0;
+  unsigned long long done = 0;
+  __syncthreads();
+  while (done < n_moves) {
+    const bool live = done + rank < n_moves;
+    int o = -2;
+    if (live) o = spec_eval<P, Real, LAYOUT>(S, st, move0 + done + rank, replica, key, step);
+    if (threadIdx.x == 0) word = o;
+    cluster_sync_all();
+    if (threadIdx.x == 0) {
+      int first = (int)K, live_n = 0, bad = 0;
+      for (unsigned r = 0; r < K; ++r) {
+        const int w = ld_cluster_int(&word, r);
+        if (w == -1) bad = 1;
+        if (w != -2) ++live_n;
+        if (w == BHMC_ACCEPT && first == (int)K) first = (int)r;
+      }
+      plan[0] = first;
+      plan[1] = first < (int)K ? first + 1 : live_n;
+      plan[2] = bad;
+    }
+    __syncthreads();
+    const int first = plan[0], nfin = plan[1], bad = plan[2];
+    if (!bad && (int)rank < nfin) {
+      if (threadIdx.x == 0) {
+        tally(&loc, o, sh.flagged);
+        if (recs) {
+          MoveRec* rec = recs + done + rank;
+          rec->i = sh.i;
+          rec->r[0] = sh.b[0];
+          rec->r[1] = sh.b[1];
+          rec->r[2] = sh.b[2];
+          rec->dE = sh.dE;
+          rec->outcome = sh.outcome;
+          rec->flagged = sh.flagged;
+        }
+      }
+      if ((int)rank == first) {
+        commit_move_block(S, st);
+        if (threadIdx.x == 0) *S.energy += sh.dE;
+      }
+    }
+    cluster_sync_all();  // the tree is final before the next step, and `word` is read
+    if (bad) break;
+    done += (unsigned long long)nfin;
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->moves), (unsigned long long)loc.moves);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->accepted), (unsigned long long)loc.accepted);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->rej_energy), (unsigned long long)loc.rej_energy);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->rej_domain), (unsigned long long)loc.rej_domain);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->rej_overlap), (unsigned long long)loc.rej_overlap);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->rej_capacity), (unsigned long long)loc.rej_capacity);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&stats->flagged), (unsigned long long)loc.flagged);
+    if (rank == 0) stats->energy = *S.energy;
+  }
+}
+
 }  // namespace bhmc

@@ -1,0 +1,90 @@
+"""The speculative multi-proposal chain (one thread-block cluster per chain,
+trials m .. m+K-1 evaluated at once, kept up to the first acceptance) must be
+the sequential chain: the same records as the one-launch-per-move path, move
+for move, and the oracle's chain within the decision band."""
+import numpy as np
+import pytest
+
+from paper_1305_1825_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL, FLOOR32 = 1e-5, 5e-7
+
+
+@pytest.fixture(scope="module")
+def bh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1825_gb300 import bhmc
+    return bhmc
+
+
+def _oracle(oracle_mod, wl):
+    return oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+
+
+def _same_records(a, b):
+    for f in ("i", "r_new", "dE", "outcome", "flagged"):
+        assert np.array_equal(a[f], b[f]), f
+
+
+@pytest.mark.parametrize("kind", ["colloid", "edl-hard", "edl-fixed-depth"])
+@pytest.mark.parametrize("proposals", [1, 2, 4, 8])
+def test_spec_chain_equals_sequential_chain(bh, kind, proposals):
+    if kind == "colloid":
+        wl = W.colloid(n=2000, seed=41)
+    elif kind == "edl-hard":
+        wl = W.edl_hard(n=800, seed=8)
+    else:
+        wl = W.edl_hard(n=800, seed=8, Lmax=6)
+    seq = bh.Context(wl, warps=8, layout=1)
+    spec = bh.Context(wl, warps=8, layout=1)
+    st0, r0 = seq.step_mc(1500, wl["step"], seed=23, records=True)
+    st1, r1 = spec.step_mc_spec(1500, wl["step"], seed=23, proposals=proposals, records=True)
+    _same_records(r0, r1)
+    for f in ("moves", "accepted", "rej_energy", "rej_domain", "rej_overlap", "rej_capacity", "flagged"):
+        assert getattr(st0, f) == getattr(st1, f), f
+    assert st0.energy == st1.energy
+    assert np.array_equal(seq.charges()[1], spec.charges()[1])
+    assert seq.export_tree() == spec.export_tree()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_spec_chain_against_oracle(bh, oracle_mod, precision):
+    wl = W.edl_hard(n=800, seed=12)
+    ctx = bh.Context(wl, precision=precision, warps=8)
+    ref = _oracle(oracle_mod, wl)
+    st, rec = ctx.step_mc_spec(2000, wl["step"], seed=5, move0=100, proposals=4, records=True)
+    orec = ref.mc_run(5, 2000, step=wl["step"], m0=100)
+    floor = 1e-12 if precision else FLOOR32
+    for t in range(2000):
+        assert rec["i"][t] == orec["i"][t] and np.array_equal(rec["r_new"][t], orec["r_new"][t]), t
+        if rec["outcome"][t] != orec["outcome"][t]:
+            assert orec["flagged"][t] or rec["flagged"][t], t
+            pytest.skip("a flagged decision split the chains at move %d" % t)
+        if orec["outcome"][t] in (0, 1):
+            assert abs(rec["dE"][t] - orec["dE"][t]) <= REL * abs(orec["dE"][t]) + floor * orec["abs_sum"][t]
+    assert st.moves == 2000
+    assert np.array_equal(ctx.charges()[1], ref.charges()[1])
+    assert ctx.export_tree() == ref.export_tree()
+
+
+def test_spec_continues_a_chain_and_rejects_bad_arguments(bh):
+    wl = W.colloid(n=1500, seed=42)
+    a = bh.Context(wl, warps=8)
+    b = bh.Context(wl, warps=8)
+    a.step_mc_spec(700, 1.0, seed=9, proposals=8)
+    a.step_mc_spec(1, 1.0, seed=9, move0=700, proposals=8)
+    a.step_mc_spec(299, 1.0, seed=9, move0=701, proposals=3)
+    b.step_mc(1000, 1.0, seed=9)
+    assert np.array_equal(a.charges()[1], b.charges()[1])
+    assert a.get_energy() == b.get_energy()
+    for bad in (0, 9):
+        with pytest.raises(bh.BhmcError):
+            a.step_mc_spec(10, 1.0, seed=9, proposals=bad)
+    st, _ = a.step_mc_spec(0, 1.0, seed=9, proposals=4)
+    assert st.moves == 0
