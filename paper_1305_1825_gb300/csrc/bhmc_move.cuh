@@ -1194,10 +1194,15 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned
                                                              bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   __shared__ int word;       // this CTA's outcome in the current step (-2: no move, -1: error)
-  __shared__ int plan[3];    // first accepted rank, moves made final, error
+  __shared__ int plan[4];    // first accepted rank, moves made final, error, commit error
+  __shared__ int cerr;       // the error word after this CTA's commit
   MoveSh& sh = st.sh;
   const unsigned rank = cluster_rank(), K = cluster_size();
-  if (*(volatile int*)S.err) return;  // stable during the launch: every CTA returns
+  // every CTA reads the error word before the barrier, where none of them can
+  // have set it yet, so all return together or none does
+  const int err0 = *(volatile int*)S.err;
+  cluster_sync_all();
+  if (err0) return;
   init_tables(sh, S.K);
   bhmc_mc_stats loc;
   loc.moves = loc.accepted = loc.rej_energy = loc.rej_domain = loc.rej_overlap = loc.rej_capacity =
@@ -1240,11 +1245,17 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned
       }
       if ((int)rank == first) {
         commit_move_block(S, st);
-        if (threadIdx.x == 0) *S.energy += sh.dE;
+        if (threadIdx.x == 0) {
+          *S.energy += sh.dE;
+          cerr = *(volatile int*)S.err;
+        }
       }
     }
     cluster_sync_all();  // the tree is final before the next step, and `word` is read
     if (bad) break;
+    if (threadIdx.x == 0) plan[3] = first < (int)K ? ld_cluster_int(&cerr, (unsigned)first) : 0;
+    __syncthreads();
+    if (plan[3]) break;  // the commit failed (pool exhausted): every CTA stops here
     done += (unsigned long long)nfin;
   }
   if (threadIdx.x == 0) {
