@@ -442,6 +442,15 @@ def _batched_moves(bh, systems, seeds, warps, layout, moves):
     return len(systems) * moves / (ms / 1e3), acc
 
 
+def _spec_batched_moves(bh, systems, seeds, warps, layout, moves, proposals):
+    b = bh.Batch(systems, warps=warps, layout=layout)
+    step = systems[0].get("step", 1.0)
+    b.step_mc_spec(moves // 4, step, seeds, proposals=proposals)
+    ms, _ = _ev_time(lambda: b.step_mc_spec(moves, step, seeds, move0=moves // 4, proposals=proposals))
+    b.close()
+    return len(systems) * moves / (ms / 1e3)
+
+
 def _oracle_moves(wl, seed, moves, budget_s):
     import oracle
     ref = oracle.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
@@ -570,8 +579,13 @@ def run_suite(args):
             systems = [W.edl_hard(n=n, seed=8000 + r, Lmax=Lmax) for r in range(reps)]
             rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps,
                                          bh.LAYOUT_AOS, 1000 if n <= 1000 else 400)
+            spec = {}
+            if reps * 8 <= 152:  # few replicas: a cluster of K CTAs per replica
+                for k in (4, 8):
+                    spec["gpu_batched_%d_replicas_clusters_of_%d_moves_per_s" % (reps, k)] = _spec_batched_moves(
+                        bh, systems, [8000 + r for r in range(reps)], args.warps, bh.LAYOUT_AOS, 4000, k)
             del systems
-            emit({"suite": "edl-hard-N%d" % n, "tree": "fixed L_max=%d" % Lmax if Lmax else "adaptive C=8",
+            emit({"suite": "edl-hard-N%d" % n, "tree": "fixed L_max=%d" % Lmax if Lmax else "adaptive C=8", **spec,
                   "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
                   "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
                   "acceptance": acc,

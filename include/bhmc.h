@@ -261,6 +261,15 @@ bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, 
 bhmc_status bhmc_batch_step_mc(bhmc_batch* batch, uint64_t n_moves, double step,
                                const uint64_t* seeds, uint64_t move0, bhmc_mc_stats* stats);
 
+/* The same chains as bhmc_batch_step_mc, each on its own thread-block cluster
+   of `proposals` CTAs evaluating that many trials per step (as
+   bhmc_step_mc_spec), all replicas in one launch of replicas x proposals CTAs.
+   For batches too small to fill the GPU with one CTA per replica.  EINVAL for
+   proposals outside 1..BHMC_MAX_PROPOSALS. */
+bhmc_status bhmc_batch_step_mc_spec(bhmc_batch* batch, uint64_t n_moves, double step,
+                                    const uint64_t* seeds, uint64_t move0, int32_t proposals,
+                                    bhmc_mc_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,8 @@ def lib():
         L.bhmc_batch_replica.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]
         L.bhmc_batch_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
                                          C.c_uint64, C.POINTER(McStats)]
+        L.bhmc_batch_step_mc_spec.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
+                                              C.c_uint64, C.c_int32, C.POINTER(McStats)]
         _lib = L
     return _lib
 
@@ -383,6 +385,13 @@ def bhmc_batch_step_mc(h, n_rep, n_moves, step, seeds, move0=0):
     return [s.as_dict() for s in st]
 
 
+def bhmc_batch_step_mc_spec(h, n_rep, n_moves, step, seeds, move0=0, proposals=4):
+    sd = (C.c_uint64 * n_rep)(*[int(s) for s in seeds])
+    st = (McStats * n_rep)()
+    _check(lib().bhmc_batch_step_mc_spec(h, n_moves, step, sd, move0, proposals, st), "bhmc_batch_step_mc_spec")
+    return [s.as_dict() for s in st]
+
+
 # ------------------------------------------------------------------ owners
 class Context:
     """One system and its device-resident octree."""
@@ -475,6 +484,9 @@ class Batch:
 
     def step_mc(self, n_moves, step, seeds, move0=0):
         return bhmc_batch_step_mc(self.h, self.n, n_moves, step, seeds, move0)
+
+    def step_mc_spec(self, n_moves, step, seeds, move0=0, proposals=4):
+        return bhmc_batch_step_mc_spec(self.h, self.n, n_moves, step, seeds, move0, proposals)
 
     def radial_counts(self, counts, charge, r_lo, r_hi):
         bhmc_radial_counts(self.h, counts, charge, r_lo, r_hi, batch=True)

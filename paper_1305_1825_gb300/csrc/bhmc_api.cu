@@ -1095,4 +1095,44 @@ bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, con
   return BHMC_OK;
 }
 
+bhmc_status bhmc_batch_step_mc_spec(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
+                                    uint64_t move0, int32_t proposals, bhmc_mc_stats* stats) {
+  if (B)
+    for (bhmc_ctx* c : B->reps) c->w_stale = true;
+  if (!B || !seeds || !(step >= 0.0) || proposals < 1 || proposals > BHMC_MAX_PROPOSALS) return BHMC_EINVAL;
+  const int n = (int)B->reps.size();
+  for (bhmc_ctx* c : B->reps) {
+    if (c->sticky) return BHMC_ESTATE;
+    if (n_moves > 0 && c->S.n_mob < 1) return BHMC_EINVAL;
+  }
+  CK(cudaMemcpyAsync(B->d_seeds, seeds, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  B->h_args->n_moves = n_moves;
+  B->h_args->move0 = move0;
+  B->h_args->step = step;
+  B->h_args->seeds = B->d_seeds;
+  B->h_args->order = B->d_order;
+  CK(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BatchArgs), cudaMemcpyHostToDevice, B->stream));
+  CK(cudaMemsetAsync(B->d_stats, 0, sizeof(bhmc_mc_stats) * n, B->stream));
+  if (n_moves) {
+    const cudaError_t e = by_p(B->p, [&](auto PC) {
+      return launch_spec_batch<PC.value>(B->reps[0]->S, B->warps, proposals, B->d_views, n, B->d_args, B->d_stats,
+                                         B->stream);
+    });
+    if (e != cudaSuccess) {
+      for (bhmc_ctx* c : B->reps) c->sticky = BHMC_ECUDA;
+      return BHMC_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(B->h_stats, B->d_stats, sizeof(bhmc_mc_stats) * n, cudaMemcpyDeviceToHost, B->stream));
+  bhmc_status rc = BHMC_OK;
+  for (bhmc_ctx* c : B->reps) {
+    bhmc_status e = sync_err(c);
+    if (e != BHMC_OK && rc == BHMC_OK) rc = e;
+  }
+  if (rc != BHMC_OK) return rc;
+  if (stats) std::memcpy(stats, B->h_stats, sizeof(bhmc_mc_stats) * n);
+  return BHMC_OK;
+}
+
 }  // extern "C"

@@ -84,6 +84,37 @@ cudaError_t launch_spec<BHMC_P>(const SysDev& S, int warps, int proposals, unsig
                         rec, stats);
 }
 
+template <typename Kern>
+static cudaError_t launch_cluster_batch(Kern kern, int proposals, int warps, int n_rep, cudaStream_t st,
+                                        const SysDev* views, const BatchArgs* args, bhmc_mc_stats* stats) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(proposals * n_rep), 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * warps), 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)proposals;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, views, n_rep, args, stats);
+}
+
+template <>
+cudaError_t launch_spec_batch<BHMC_P>(const SysDev& S0, int warps, int proposals, const SysDev* views, int n_rep,
+                                      const BatchArgs* args, bhmc_mc_stats* stats, cudaStream_t st) {
+  if (S0.prec == BHMC_PREC_F64)
+    return launch_cluster_batch(k_spec_batch<BHMC_P, double, BHMC_LAYOUT_SOA>, proposals, warps, n_rep, st, views,
+                                args, stats);
+  if (S0.layout == BHMC_LAYOUT_AOS)
+    return launch_cluster_batch(k_spec_batch<BHMC_P, float, BHMC_LAYOUT_AOS>, proposals, warps, n_rep, st, views,
+                                args, stats);
+  return launch_cluster_batch(k_spec_batch<BHMC_P, float, BHMC_LAYOUT_SOA>, proposals, warps, n_rep, st, views,
+                              args, stats);
+}
+
 template <>
 cudaError_t launch_batch<BHMC_P>(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
                                  const BatchArgs* args, int* next, bhmc_mc_stats* stats,

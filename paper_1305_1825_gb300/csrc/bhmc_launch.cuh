@@ -25,6 +25,9 @@ cudaError_t launch_spec(const SysDev& S, int warps, int proposals, unsigned long
                         unsigned long long n_moves, unsigned long long seed, double step, MoveRec* rec,
                         bhmc_mc_stats* stats, cudaStream_t st);
 template <int P>
+cudaError_t launch_spec_batch(const SysDev& S0, int warps, int proposals, const SysDev* views, int n_rep,
+                              const BatchArgs* args, bhmc_mc_stats* stats, cudaStream_t st);
+template <int P>
 cudaError_t launch_batch(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
                          const BatchArgs* args, int* next, bhmc_mc_stats* stats, cudaStream_t st);
 template <int P>
@@ -53,6 +56,8 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
   template <> cudaError_t launch_spec<P>(const SysDev&, int, int, unsigned long long,         \
                                         unsigned long long, unsigned long long, double, MoveRec*,  \
                                         bhmc_mc_stats*, cudaStream_t);                             \
+  template <> cudaError_t launch_spec_batch<P>(const SysDev&, int, int, const SysDev*, int,   \
+                                              const BatchArgs*, bhmc_mc_stats*, cudaStream_t);  \
   template <> cudaError_t launch_batch<P>(const SysDev&, int, const SysDev*, int, int,       \
                                               const BatchArgs*, int*, bhmc_mc_stats*,            \
                                               cudaStream_t);                                     \

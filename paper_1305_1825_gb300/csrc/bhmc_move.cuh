@@ -1184,14 +1184,12 @@ __device__ int spec_eval(const SysDev& S, MoveStore& st, unsigned long long m, u
   return sh.outcome;
 }
 
-// One chain of n_moves trial moves from move0 on a cluster of K CTAs (see
-// above).  stats must be zeroed by the caller; recs (may be null) receives
+// One chain of n_moves trial moves from move0 on this cluster of K CTAs (see
+// above).  *stats must be zeroed by the caller; recs (may be null) receives
 // one record per move.
 template <int P, typename Real, int LAYOUT>
-__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned long long move0,
-                                                             unsigned long long n_moves, unsigned replica,
-                                                             uint2 key, double step, MoveRec* recs,
-                                                             bhmc_mc_stats* stats) {
+__device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned long long n_moves,
+                           unsigned replica, uint2 key, double step, MoveRec* recs, bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   __shared__ int word;       // this CTA's outcome in the current step (-2: no move, -1: error)
   __shared__ int plan[4];    // first accepted rank, moves made final, error, commit error
@@ -1268,6 +1266,28 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned
     atomicAdd(reinterpret_cast<unsigned long long*>(&stats->flagged), (unsigned long long)loc.flagged);
     if (rank == 0) stats->energy = *S.energy;
   }
+}
+
+template <int P, typename Real, int LAYOUT>
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec(SysDev S, unsigned long long move0,
+                                                             unsigned long long n_moves, unsigned replica,
+                                                             uint2 key, double step, MoveRec* recs,
+                                                             bhmc_mc_stats* stats) {
+  spec_chain<P, Real, LAYOUT>(S, move0, n_moves, replica, key, step, recs, stats);
+}
+
+// Replica r of a batch on cluster r (grid = replicas x K CTAs, clusters of K).
+template <int P, typename Real, int LAYOUT>
+__global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_spec_batch(const SysDev* views, int n_rep,
+                                                                   const BatchArgs* args, bhmc_mc_stats* stats) {
+  __shared__ SysDev S;
+  const int r = (int)(blockIdx.x / cluster_size());
+  if (r >= n_rep) return;  // the whole cluster
+  if (threadIdx.x == 0) S = views[r];
+  __syncthreads();
+  const unsigned long long seed = args->seeds[r];
+  spec_chain<P, Real, LAYOUT>(S, args->move0, args->n_moves, (unsigned)r,
+                              make_uint2((unsigned)seed, (unsigned)(seed >> 32)), args->step, nullptr, stats + r);
 }
 
 }  // namespace bhmc

@@ -88,3 +88,21 @@ def test_spec_continues_a_chain_and_rejects_bad_arguments(bh):
             a.step_mc_spec(10, 1.0, seed=9, proposals=bad)
     st, _ = a.step_mc_spec(0, 1.0, seed=9, proposals=4)
     assert st.moves == 0
+
+
+@pytest.mark.parametrize("proposals", [1, 4, 8])
+def test_batch_spec_equals_batch_chain(bh, proposals):
+    """Every replica of a cluster-per-replica batch follows the replica's chain of
+    the one-CTA-per-replica batch (same per-replica statistics and final state)."""
+    systems = [W.edl_hard(n=n, seed=70 + k) for k, n in enumerate((300, 800, 500, 650, 400))]
+    a = bh.Batch(systems, warps=8)
+    b = bh.Batch(systems, warps=8)
+    seeds = [500 + r for r in range(len(systems))]
+    sa = a.step_mc(600, 2.0, seeds, move0=3)
+    sb = b.step_mc_spec(600, 2.0, seeds, move0=3, proposals=proposals)
+    for r in range(len(systems)):
+        for f in ("moves", "accepted", "rej_energy", "rej_domain", "rej_overlap", "rej_capacity", "flagged"):
+            assert sa[r][f] == sb[r][f], (r, f)
+        assert sa[r]["energy"] == sb[r]["energy"]
+        assert np.array_equal(a.replica(r).charges()[1], b.replica(r).charges()[1])
+        assert a.replica(r).export_tree() == b.replica(r).export_tree()
