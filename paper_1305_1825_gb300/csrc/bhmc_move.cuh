@@ -1153,12 +1153,20 @@ template <int P, typename Real, int LAYOUT>
 __device__ int spec_eval(const SysDev& S, MoveStore& st, unsigned long long m, unsigned replica, uint2 key,
                          double step) {
   MoveSh& sh = st.sh;
-  propose(S, sh, m, replica, key, step, 0);
+  if (sh.nxt_m == m) {  // set up during the previous step's commit
+    constexpr int n = (int)(sizeof(MoveSetup) / sizeof(int));
+    int* dst = reinterpret_cast<int*>(static_cast<MoveSetup*>(&sh));
+    const int* src = reinterpret_cast<const int*>(&sh.nxt);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+  } else {
+    propose(S, sh, m, replica, key, step, 0);
+    __syncthreads();
+    setup_roles(S, sh, 0);
+    __syncthreads();
+    setup_finish(S, sh, 0);
+  }
   __syncthreads();
-  setup_roles(S, sh, 0);
-  __syncthreads();
-  setup_finish(S, sh, 0);
-  __syncthreads();
+  if (threadIdx.x == 0) sh.nxt_m = ~0ULL;
   if (sh.outcome < 0) {
     eval_move<P, Real, LAYOUT>(S, st, true);
     if (sh.cnt[0][4]) {
@@ -1194,6 +1202,7 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
   __shared__ int word;       // this CTA's outcome in the current step (-2: no move, -1: error)
   __shared__ int plan[4];    // first accepted rank, moves made final, error, commit error
   __shared__ int cerr;       // the error word after this CTA's commit
+  __shared__ int cion;       // the ion this CTA's commit moved
   MoveSh& sh = st.sh;
   const unsigned rank = cluster_rank(), K = cluster_size();
   // every CTA reads the error word before the barrier, where none of them can
@@ -1202,10 +1211,12 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
   cluster_sync_all();
   if (err0) return;
   init_tables(sh, S.K);
+  if (threadIdx.x == 0) sh.nxt_m = ~0ULL;
   bhmc_mc_stats loc;
   loc.moves = loc.accepted = loc.rej_energy = loc.rej_domain = loc.rej_overlap = loc.rej_capacity =
       loc.flagged = 0;
   unsigned long long done = 0;
+  const int warp = threadIdx.x >> 5;
   __syncthreads();
   while (done < n_moves) {
     const bool live = done + rank < n_moves;
@@ -1227,6 +1238,10 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
     }
     __syncthreads();
     const int first = plan[0], nfin = plan[1], bad = plan[2];
+    // this CTA's trial of the next step, set up while the commit runs (valid
+    // unless it draws the ion that the commit moves)
+    const unsigned long long mn = move0 + done + (unsigned long long)nfin + rank;
+    const bool ahead = !bad && done + (unsigned long long)nfin + rank < n_moves;
     if (!bad && (int)rank < nfin) {
       if (threadIdx.x == 0) {
         tally(&loc, o, sh.flagged);
@@ -1241,17 +1256,41 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
           rec->flagged = sh.flagged;
         }
       }
-      if ((int)rank == first) {
-        commit_move_block(S, st);
+    }
+    if (!bad && (int)rank == first) {
+      const bool split = ahead && blockDim.x == 256;
+      if (split && warp >= 5) {  // warps 5-7: the next trial's setup
+        propose(S, sh.nxt, mn, replica, key, step, 5);
+        bar_ahead();
+        setup_roles(S, sh.nxt, 5);
+        bar_ahead();
+        setup_finish(S, sh.nxt, 5);
+        if (threadIdx.x == 160) sh.nxt_m = mn;
+      } else {
+        commit_move_block(S, st, split ? 160 : 0, split ? 2 : 0);
         if (threadIdx.x == 0) {
           *S.energy += sh.dE;
           cerr = *(volatile int*)S.err;
+          cion = (int)sh.i;
         }
       }
+    } else if (ahead) {
+      propose(S, sh.nxt, mn, replica, key, step, 0);
+      __syncthreads();
+      setup_roles(S, sh.nxt, 0);
+      __syncthreads();
+      setup_finish(S, sh.nxt, 0);
+      if (threadIdx.x == 0) sh.nxt_m = mn;
     }
+    __syncthreads();
     cluster_sync_all();  // the tree is final before the next step, and `word` is read
     if (bad) break;
-    if (threadIdx.x == 0) plan[3] = first < (int)K ? ld_cluster_int(&cerr, (unsigned)first) : 0;
+    if (threadIdx.x == 0) {
+      plan[3] = first < (int)K ? ld_cluster_int(&cerr, (unsigned)first) : 0;
+      // a setup that read the moved ion's old position is redone
+      if (first < (int)K && sh.nxt_m != ~0ULL && (int)sh.nxt.i == ld_cluster_int(&cion, (unsigned)first))
+        sh.nxt_m = ~0ULL;
+    }
     __syncthreads();
     if (plan[3]) break;  // the commit failed (pool exhausted): every CTA stops here
     done += (unsigned long long)nfin;
