@@ -105,12 +105,15 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   // pass's slot loads are issued before the multipole work.
   auto run_items = [&](int tm_, int td_) {
     const int per = nth >> lg;
-    const int kk = tid & (cp - 1);
+    // direct lanes counted from the top thread down, so that the low threads,
+    // which take the second multipole items of a busy round, get none
+    const int rt = nth - 1 - tid;
+    const int kk = rt & (cp - 1);
     uint2 di0 = make_uint2(0u, 0u);
     float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
     bool have0 = false;
-    if ((tid >> lg) < td_) {
-      di0 = B.di[tid >> lg];
+    if ((rt >> lg) < td_) {
+      di0 = B.di[rt >> lg];
       if (kk < (int)((di0.y >> 4) & 0xffffu)) {
         const int slot = (int)di0.x * SC + kk;
         sa0 = S.sA[slot];
@@ -138,7 +141,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       if (hc && ((di0.y & 2u) || (di0.y >> 30))) ovl |= hc_slot(S, T, sa0, sb0);
     }
     for (int base = per; base < td_; base += per) {
-      const int item = base + (tid >> lg);
+      const int item = base + (rt >> lg);
       if (item < td_) {
         const uint2 di = B.di[item];
         if (kk < (int)((di.y >> 4) & 0xffffu)) {
