@@ -105,9 +105,11 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   // pass's slot loads are issued before the multipole work.
   auto run_items = [&](int tm_, int td_) {
     const int per = nth >> lg;
-    // direct lanes counted from the top thread down, so that the low threads,
-    // which take the second multipole items of a busy round, get none
-    const int rt = nth - 1 - tid;
+    // multipole items go from the top thread down and direct lanes from the
+    // bottom up: the threads that take a busy round's second multipole item
+    // get no direct term and, when the next round pops fewer groups than the
+    // block has, no cluster to classify either
+    const int rt = tid;
     const int kk = rt & (cp - 1);
     uint2 di0 = make_uint2(0u, 0u);
     float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
@@ -121,7 +123,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
         have0 = true;
       }
     }
-    for (int k = tid; k < tm_; k += nth) {
+    for (int k = nth - 1 - tid; k < tm_; k += nth) {
       const unsigned it = B.mi[k];
       const int s = (int)(it & 3u);
       if (GRAD) {
