@@ -109,13 +109,12 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     // bottom up: the threads that take a busy round's second multipole item
     // get no direct term and, when the next round pops fewer groups than the
     // block has, no cluster to classify either
-    const int rt = tid;
-    const int kk = rt & (cp - 1);
+    const int kk = tid & (cp - 1);
     uint2 di0 = make_uint2(0u, 0u);
     float4 sa0 = make_float4(0.f, 0.f, 0.f, 0.f), sb0 = sa0;
     bool have0 = false;
-    if ((rt >> lg) < td_) {
-      di0 = B.di[rt >> lg];
+    if ((tid >> lg) < td_) {
+      di0 = B.di[tid >> lg];
       if (kk < (int)((di0.y >> 4) & 0xffffu)) {
         const int slot = (int)di0.x * SC + kk;
         sa0 = S.sA[slot];
@@ -143,7 +142,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
       if (hc && ((di0.y & 2u) || (di0.y >> 30))) ovl |= hc_slot(S, T, sa0, sb0);
     }
     for (int base = per; base < td_; base += per) {
-      const int item = base + (rt >> lg);
+      const int item = base + (tid >> lg);
       if (item < td_) {
         const uint2 di = B.di[item];
         if (kk < (int)((di.y >> 4) & 0xffffu)) {
