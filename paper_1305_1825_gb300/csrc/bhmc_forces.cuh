@@ -7,8 +7,8 @@
 //   phi_i and the target gradient grad phi_i (d/dx T_n(r_A - x) =
 //   -(n_c + 1) T_{n+e_c}); the cluster adjoints lambda_A^n += q_i T_n(r_A - r_i);
 //   direct pairs' source terms psi_j += q_i/r and s_j += -q_i q_j (r_j - r_i)/r^3.
-//   Lanes reduce their contributions to one value per warp before a single FP64
-//   atomic add.
+//   The warp's lanes reduce-scatter their contributions, so that each sum is
+//   added by one FP64 atomic from the lane that holds it.
 // Pass 2 (k_forces_push): every charge k walks the clusters containing it and
 //   collects sum_n lambda_A^n (r_k - r_A)^n (for dE/dq_k) and
 //   q_k sum_n lambda_A^n d/dr_k (r_k - r_A)^n (for dE/dr_k).
@@ -18,11 +18,24 @@
 
 namespace bhmc {
 
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v) {
+// Sums over the 32 lanes of v[0..KP), scattered: afterwards lane L holds the
+// sums of terms M L .. M L + M - 1 in v[0..M), M = KP / 32.  Recursive halving:
+// at each of five steps a lane keeps half of its terms and adds its partner's
+// values of them, KP - M shuffles in all (a butterfly per term takes 5 KP).
+template <int KP, int N, typename R>
+__device__ __forceinline__ void warp_reduce_scatter(R (&v)[N], int lane) {
+  static_assert(KP % 32 == 0 && KP <= N, "KP must be a multiple of 32 within the array");
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int st = 0; st < 5; ++st) {
+    const int o = 16 >> st, half = KP >> (st + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const R a = v[j], b = v[j + half];
+      const R keep = up ? b : a, send = up ? a : b;
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
 }
 
 template <int P, typename Real, int LAYOUT>
@@ -31,6 +44,8 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
                                                          int* err) {
   constexpr int K = nterms(P);
   constexpr int K1 = nterms(P + 1);
+  constexpr int KP = (K + 31) / 32 * 32;            // adjoint terms padded for the reduce-scatter
+  constexpr int NT = K1 > KP ? K1 : KP;
   __shared__ EnergyStack stk[4];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -106,7 +121,7 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
         if (__any_sync(FULL, mul)) {
           // Taylor coefficients to order p + 1 at R = r_A - x (an accepted cluster
           // never holds its own target, so M' = M)
-          Real Tc[K1];
+          Real Tc[NT];
           {
             Real rx, ry, rz;
             if (sizeof(Real) == 4) {
@@ -118,7 +133,7 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
               ry = (Real)__dsub_rn((double)a.y, x[1]);
               rz = (Real)__dsub_rn((double)a.z, x[2]);
             }
-            taylor<P + 1, Real>(rx, ry, rz, Tc);
+            taylor<P + 1, Real>(rx, ry, rz, *reinterpret_cast<Real(*)[K1]>(&Tc[0]));
           }
           Real v = 0, d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
@@ -139,16 +154,24 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
                 d0 -= Real(n1 + 1) * Tc[tidx(n1 + 1, n2, n3)] * m;
                 d1 -= Real(n2 + 1) * Tc[tidx(n1, n2 + 1, n3)] * m;
                 d2 -= Real(n3 + 1) * Tc[tidx(n1, n2, n3 + 1)] * m;
-                // cluster adjoint: the warp's contributions summed in the
-                // traversal precision, one FP64 atomic per term and warp
-                const Real l = warp_sum<Real>(mul ? (Real)qi * Tc[t] : Real(0));
-                if (lane == 0) atomicAdd(&lam[(size_t)node * K + t], (double)l);
               }
           if (mul) {
             phi.add(v);
             g0.add(d0);
             g1.add(d1);
             g2.add(d2);
+          }
+          // cluster adjoint: the warp's contributions q_i T_n summed in the
+          // traversal precision (reduce-scatter), then one FP64 atomic per
+          // term, issued by the lane that holds its sum
+          const Real qm = mul ? (Real)qi : Real(0);
+#pragma unroll
+          for (int t = 0; t < KP; ++t) Tc[t] = t < K ? qm * Tc[t] : Real(0);
+          warp_reduce_scatter<KP>(Tc, lane);
+#pragma unroll
+          for (int u = 0; u < KP / 32; ++u) {
+            const int t = (KP / 32) * lane + u;
+            if (t < K && Tc[u] != Real(0)) atomicAdd(&lam[(size_t)node * K + t], (double)Tc[u]);
           }
         }
         const unsigned mo = __ballot_sync(FULL, opn), mf = __ballot_sync(FULL, fdv);
@@ -162,46 +185,56 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
           ++top;
         }
         if (__any_sync(FULL, dir)) {
-          for (int k = 0; k < b.y; ++k) {
-            const float4 sa = S.sA[node * SC + k];
-            const float4 sb = S.sB[node * SC + k];
-            const int j = __float_as_int(sb.w);
-            Real cp = 0, c0 = 0, c1 = 0, c2 = 0;
-            if (dir && j != i) {
-              Real ex, ey, ez, qj;
-              if (sizeof(Real) == 4) {
-                ex = (Real)((sa.x - hi[0]) + (sb.x - lo[0]));
-                ey = (Real)((sa.y - hi[1]) + (sb.y - lo[1]));
-                ez = (Real)((sa.z - hi[2]) + (sb.z - lo[2]));
-                qj = (Real)sa.w;
-              } else {
-                ex = (Real)(S.px[j] - x[0]);
-                ey = (Real)(S.py[j] - x[1]);
-                ez = (Real)(S.pz[j] - x[2]);
-                qj = (Real)S.pq[j];
+          // eight slots at a time; their source terms (psi_j and the three
+          // components of s_j) summed over the warp by one reduce-scatter,
+          // after which lane 4u + c holds component c of slot u
+          for (int k0 = 0; k0 < b.y; k0 += 8) {
+            Real w[32];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              Real cp = 0, c0 = 0, c1 = 0, c2 = 0;
+              const int k = k0 + u;
+              if (k < b.y) {
+                const float4 sa = S.sA[node * SC + k];
+                const float4 sb = S.sB[node * SC + k];
+                const int j = __float_as_int(sb.w);
+                if (dir && j != i) {
+                  Real ex, ey, ez, qj;
+                  if (sizeof(Real) == 4) {
+                    ex = (Real)((sa.x - hi[0]) + (sb.x - lo[0]));
+                    ey = (Real)((sa.y - hi[1]) + (sb.y - lo[1]));
+                    ez = (Real)((sa.z - hi[2]) + (sb.z - lo[2]));
+                    qj = (Real)sa.w;
+                  } else {
+                    ex = (Real)(S.px[j] - x[0]);
+                    ey = (Real)(S.py[j] - x[1]);
+                    ez = (Real)(S.pz[j] - x[2]);
+                    qj = (Real)S.pq[j];
+                  }
+                  const Real r2 = ex * ex + ey * ey + ez * ez;
+                  const Real rinv = rsqrt_t<Real>(r2);
+                  const Real r3inv = rinv * rinv * rinv;
+                  phi.add(qj * rinv);
+                  g0.add(qj * ex * r3inv);
+                  g1.add(qj * ey * r3inv);
+                  g2.add(qj * ez * r3inv);
+                  const Real qr = (Real)qi;
+                  cp = qr * rinv;
+                  c0 = -qr * qj * ex * r3inv;
+                  c1 = -qr * qj * ey * r3inv;
+                  c2 = -qr * qj * ez * r3inv;
+                }
               }
-              const Real r2 = ex * ex + ey * ey + ez * ez;
-              const Real rinv = rsqrt_t<Real>(r2);
-              const Real r3inv = rinv * rinv * rinv;
-              phi.add(qj * rinv);
-              g0.add(qj * ex * r3inv);
-              g1.add(qj * ey * r3inv);
-              g2.add(qj * ez * r3inv);
-              const Real qr = (Real)qi;
-              cp = qr * rinv;
-              c0 = -qr * qj * ex * r3inv;
-              c1 = -qr * qj * ey * r3inv;
-              c2 = -qr * qj * ez * r3inv;
+              w[4 * u + 0] = cp;
+              w[4 * u + 1] = c0;
+              w[4 * u + 2] = c1;
+              w[4 * u + 3] = c2;
             }
-            cp = warp_sum<Real>(cp);
-            c0 = warp_sum<Real>(c0);
-            c1 = warp_sum<Real>(c1);
-            c2 = warp_sum<Real>(c2);
-            if (lane == 0 && (cp != Real(0) || c0 != Real(0) || c1 != Real(0) || c2 != Real(0))) {
-              atomicAdd(&psi[j], (double)cp);
-              atomicAdd(&src[3 * j + 0], (double)c0);
-              atomicAdd(&src[3 * j + 1], (double)c1);
-              atomicAdd(&src[3 * j + 2], (double)c2);
+            warp_reduce_scatter<32>(w, lane);
+            const int u = lane >> 2, c = lane & 3;
+            if (k0 + u < b.y && w[0] != Real(0)) {
+              const int j = __float_as_int(S.sB[node * SC + k0 + u].w);
+              atomicAdd(c == 0 ? &psi[j] : &src[3 * j + c - 1], (double)w[0]);
             }
           }
         }
