@@ -668,9 +668,11 @@ def run_suite(args):
         b.step_mc(100, 1.0, [9])
         ms_b, _ = _ev_time(lambda: b.step_mc(4000, 1.0, [9], move0=100))
         b.close()
+        rate4, acc4 = _spec_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 4000, 4)
         emit({"suite": "large-N1e6", "theta": 0.5, "p": 6, "C": 8, "charges": 2000001,
               "gpu_plain_moves_per_s": 500 / (ms / 1e3),
-              "gpu_persistent_1_replica_moves_per_s": 4000 / (ms_b / 1e3)})
+              "gpu_persistent_1_replica_moves_per_s": 4000 / (ms_b / 1e3),
+              "gpu_cluster_4_proposals_moves_per_s": rate4, "acceptance": acc4})
     return lines
 
 
