@@ -131,6 +131,11 @@ bhmc_status bhmc_destroy(bhmc_ctx* ctx);
 bhmc_status bhmc_n_charges(const bhmc_ctx* ctx, int64_t* n);
 /* Copy current charges and positions (xyz interleaved) to host or device buffers. */
 bhmc_status bhmc_get_charges(bhmc_ctx* ctx, double* q, double* xyz, int32_t flags);
+/* Positions only (n_charges x 3, interleaved), host or device buffer per flags. */
+bhmc_status bhmc_get_positions(bhmc_ctx* ctx, double* xyz, int32_t flags);
+/* Interaction-list counters of the last successful bhmc_delta_energy or
+   bhmc_energy_counters call on this context (zeros before any). */
+bhmc_status bhmc_get_counters(bhmc_ctx* ctx, bhmc_counters* out);
 
 /* Energy difference of moving mobile ion i (and its image) to r_new (Sec. 1:
    V_i evaluated before and after the displacement; Sec. 3.2 traversal with the

@@ -79,6 +79,8 @@ def lib():
         L.bhmc_destroy.argtypes = [C.c_void_p]
         L.bhmc_n_charges.argtypes = [C.c_void_p, _i64p]
         L.bhmc_get_charges.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+        L.bhmc_get_positions.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+        L.bhmc_get_counters.argtypes = [C.c_void_p, C.POINTER(Counters)]
         L.bhmc_delta_energy.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, C.POINTER(Counters)]
         L.bhmc_commit_move.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.bhmc_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
@@ -315,6 +317,19 @@ def bhmc_get_charges(h):
     return q, x
 
 
+def bhmc_get_positions(h):
+    n = bhmc_n_charges(h)
+    x = np.zeros((n, 3))
+    _check(lib().bhmc_get_positions(h, C.c_void_p(x.ctypes.data), HOST_PTRS), "bhmc_get_positions")
+    return x
+
+
+def bhmc_get_counters(h):
+    c = Counters()
+    _check(lib().bhmc_get_counters(h, C.byref(c)), "bhmc_get_counters")
+    return c
+
+
 def bhmc_export_tree(h, K=None):
     """{(depth, key): (is_leaf, count, members or None)} and, if K is given, moments per key."""
     n = bhmc_n_charges(h)
@@ -458,6 +473,12 @@ class Context:
 
     def charges(self):
         return bhmc_get_charges(self.h)
+
+    def positions(self):
+        return bhmc_get_positions(self.h)
+
+    def counters(self):
+        return bhmc_get_counters(self.h)
 
     def export_tree(self, moments=False):
         return bhmc_export_tree(self.h, self.K if moments else None)

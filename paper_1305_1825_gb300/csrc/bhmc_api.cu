@@ -39,6 +39,7 @@ struct bhmc_ctx {
   int sticky = 0;
   bool borrowed = false;
   bool w_stale = true;  // W32 not refreshed since the moments last changed
+  bhmc_counters last = {0, 0, 0, 0};  // counters of the last delta_energy / energy_counters
 };
 
 struct bhmc_batch {
@@ -564,13 +565,23 @@ bhmc_status bhmc_delta_energy(bhmc_ctx* ctx, int64_t i, const double r_new[3], d
   if (hio->delta.err) return (bhmc_status)hio->delta.err;
   if (hio->delta.status) return (bhmc_status)hio->delta.status;
   *dE = hio->delta.dE;
-  if (counters) {
-    counters->visited = hio->delta.cnt[0];
-    counters->accepted = hio->delta.cnt[1];
-    counters->pairs = hio->delta.cnt[2];
-    counters->mac_fp64 = hio->delta.cnt[3];
-  }
+  ctx->last.visited = hio->delta.cnt[0];
+  ctx->last.accepted = hio->delta.cnt[1];
+  ctx->last.pairs = hio->delta.cnt[2];
+  ctx->last.mac_fp64 = hio->delta.cnt[3];
+  if (counters) *counters = ctx->last;
   return BHMC_OK;
+}
+
+bhmc_status bhmc_get_counters(bhmc_ctx* ctx, bhmc_counters* out) {
+  if (!ctx || !out) return BHMC_EINVAL;
+  *out = ctx->last;
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_get_positions(bhmc_ctx* ctx, double* xyz, int32_t flags) {
+  if (!xyz) return BHMC_EINVAL;
+  return bhmc_get_charges(ctx, nullptr, xyz, flags);
 }
 
 bhmc_status bhmc_commit_move(bhmc_ctx* ctx, int64_t i, const double r_new[3]) {
@@ -816,6 +827,7 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
     total->accepted = (int64_t)hcnt[1];
     total->pairs = (int64_t)hcnt[2];
     total->mac_fp64 = 0;
+    ctx->last = *total;
   }
   return BHMC_OK;
 }

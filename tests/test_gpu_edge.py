@@ -127,3 +127,22 @@ def test_node_pool_exhaustion_is_reported(bh):
             break
     assert seen == bh.ENOMEM_POOL
     assert ctx.delta_energy(0, [0.0, 0.0, 0.0])[0] == bh.ESTATE
+
+
+def test_positions_and_last_counters(bh, oracle_mod):
+    """bhmc_get_positions equals the positions of bhmc_get_charges;
+    bhmc_get_counters returns the last evaluation's interaction-list counters."""
+    wl = W.colloid(n=800, seed=21)
+    ctx = bh.Context(wl, warps=4)
+    c0 = ctx.counters()
+    assert (c0.visited, c0.accepted, c0.pairs) == (0, 0, 0)
+    assert np.array_equal(ctx.positions(), ctx.charges()[1])
+    i = 5
+    b = wl["xyz"][i] + np.array([0.2, -0.1, 0.3])
+    rc, dE, cnt = ctx.delta_energy(i, b)
+    assert rc == 0
+    last = ctx.counters()
+    assert (last.visited, last.accepted, last.pairs) == (cnt.visited, cnt.accepted, cnt.pairs) and cnt.visited > 0
+    E, tot = ctx.energy_counters()
+    last = ctx.counters()
+    assert (last.visited, last.accepted, last.pairs) == (tot.visited, tot.accepted, tot.pairs)
