@@ -39,7 +39,10 @@ typedef enum {
   BHMC_ESTATE = 8,      /* the context holds an earlier device error */
   BHMC_ECAPACITY = 9,   /* a depth-Dmax cell would hold more than C charges */
   BHMC_ESTACK = 10,     /* a traversal stack overflowed */
-  BHMC_ESCRATCH = 11    /* problem larger than a call's fixed scratch allows */
+  BHMC_ESCRATCH = 11,   /* problem larger than a call's fixed scratch allows */
+  BHMC_ENONFINITE = 12  /* a trial's energy difference was not finite (the FP32 expansion
+                           overflowed: use BHMC_PREC_F64 or a lower order); the trial is
+                           rejected and the chain stops at the next move */
 } bhmc_status;
 
 enum { BHMC_PREC_F32 = 0, BHMC_PREC_F64 = 1 };   /* traversal arithmetic */

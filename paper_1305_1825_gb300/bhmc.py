@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-OK, EINVAL, EDOMAIN, EOVERLAP, ENOMEM, ENOMEM_POOL, ECUDA, ETIMEOUT, ESTATE, ECAPACITY, ESTACK, ESCRATCH = range(12)
+OK, EINVAL, EDOMAIN, EOVERLAP, ENOMEM, ENOMEM_POOL, ECUDA, ETIMEOUT, ESTATE, ECAPACITY, ESTACK, ESCRATCH, ENONFINITE = range(13)
 PREC_F32, PREC_F64 = 0, 1
 LAYOUT_SOA, LAYOUT_AOS = 0, 1
 HOST_PTRS, DEVICE_PTRS = 0, 1

@@ -79,6 +79,7 @@ const char* bhmc_status_string(bhmc_status s) {
     case BHMC_ECAPACITY: return "depth-Dmax cell over capacity";
     case BHMC_ESTACK: return "traversal stack overflow";
     case BHMC_ESCRATCH: return "problem larger than the call's fixed scratch";
+    case BHMC_ENONFINITE: return "non-finite energy difference (FP32 expansion overflow)";
   }
   return "unknown status";
 }

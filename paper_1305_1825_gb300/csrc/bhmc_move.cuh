@@ -808,7 +808,10 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
         int acc, fl;
         metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
         sh.flagged = fl;
-        if (!acc)
+        if (!isfinite(sh.dE)) {
+          set_err(S, BHMC_ENONFINITE);
+          sh.outcome = BHMC_REJECT_ENERGY;
+        } else if (!acc)
           sh.outcome = BHMC_REJECT_ENERGY;
         else if (capacity_violation(S, sh))
           sh.outcome = BHMC_REJECT_CAPACITY;
@@ -1180,7 +1183,10 @@ __device__ int spec_eval(const SysDev& S, MoveStore& st, unsigned long long m, u
       int acc, fl;
       metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
       sh.flagged = fl;
-      if (!acc)
+      if (!isfinite(sh.dE)) {
+        set_err(S, BHMC_ENONFINITE);
+        sh.outcome = BHMC_REJECT_ENERGY;
+      } else if (!acc)
         sh.outcome = BHMC_REJECT_ENERGY;
       else if (capacity_violation(S, sh))
         sh.outcome = BHMC_REJECT_CAPACITY;

@@ -25,6 +25,7 @@ def test_library_exports_every_declared_call():
 def test_status_strings_and_validation_without_gpu():
     from paper_1305_1825_gb300 import bhmc, workloads
     assert bhmc.bhmc_status_string(bhmc.ECAPACITY).startswith("depth-Dmax")
+    assert "non-finite" in bhmc.bhmc_status_string(bhmc.ENONFINITE)
     # invalid parameters are rejected on the host before any CUDA call
     wl = workloads.plain(n=16)
     for bad in (dict(p=11), dict(C=1), dict(theta=1.0), dict(root_side=30.0), dict(Dmax=21)):
