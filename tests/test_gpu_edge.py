@@ -146,3 +146,30 @@ def test_positions_and_last_counters(bh, oracle_mod):
     E, tot = ctx.energy_counters()
     last = ctx.counters()
     assert (last.visited, last.accepted, last.pairs) == (tot.visited, tot.accepted, tot.pairs)
+
+
+def test_checkpoint_and_resume(bh):
+    """A chain stopped after 800 moves, rebuilt from its exported charges (the
+    tree is a function of the particle set) and resumed at move 800 with its
+    running energy, follows the uninterrupted chain (decisions can differ only
+    within the flagged band, since rebuilt moments round differently)."""
+    wl = W.edl_hard(n=600, seed=31)
+    full = bh.Context(wl, warps=8)
+    _, r_full = full.step_mc(1600, 2.0, seed=4, records=True)
+    first = bh.Context(wl, warps=8)
+    first.step_mc(800, 2.0, seed=4)
+    q, x = first.charges()
+    n = wl["n_mobile"] + wl["n_fixed"]
+    resumed = bh.Context(dict(wl, q=q[:n], xyz=x[:n]), warps=8)
+    assert resumed.export_tree() == first.export_tree()
+    resumed.set_energy(first.get_energy())
+    _, r_res = resumed.step_mc(800, 2.0, seed=4, move0=800, records=True)
+    tail = r_full[800:]
+    same = tail["outcome"] == r_res["outcome"]
+    if same.all():
+        assert np.array_equal(tail["r_new"], r_res["r_new"])
+        assert np.array_equal(full.charges()[1], resumed.charges()[1])
+        assert abs(resumed.get_energy() - full.get_energy()) <= 1e-5 * float(np.abs(tail["dE"]).sum()) + 1e-9
+    else:
+        k = int(np.argmin(same))
+        assert tail["flagged"][k] or r_res["flagged"][k]
