@@ -207,6 +207,34 @@ def brute_tree(xyz, lo, side, C, Dmax):
     return out
 
 
+
+def test_moved_set_exclusion_equals_zeroed_charge(oracle_mod):
+    """The potential at a trial point with ion i excluded (moments corrected by
+    q_i (r_i - r_A)^n on i's ancestors, i skipped in leaf sums) equals the
+    treecode potential of the same tree with q_i set to zero: the tree's shape
+    depends on positions only, and with N0 = 0 a cluster left empty by the
+    exclusion contributes nothing either way.  Also with two excluded charges."""
+    rng = np.random.default_rng(2)
+    for wl in (W.plain(n=500, seed=17, C=3), W.colloid(n=400, seed=17, C=3)):
+        wl["params"]["Dmax"] = 12
+        q, x = wl["q"], wl["xyz"]
+        nm, nf = wl["n_mobile"], wl["n_fixed"]
+        s = oracle_mod.System(wl["params"], q, x, nm, nf)
+        images = bool(wl["params"]["image"])
+        for _ in range(12):
+            i, j = (int(v) for v in rng.choice(nm, 2, replace=False))
+            # an ion's image charge follows the ion's: zeroing q_i zeroes both
+            sets = ([i], [i, j]) if not images else ([i], [j])
+            for ions in sets:
+                excl = ions + ([nm + nf + k for k in ions] if images else [])
+                b = x[ions[0]] + rng.uniform(-0.6, 0.6, 3)
+                q0 = q.copy()
+                q0[ions] = 0.0
+                z = oracle_mod.System(wl["params"], q0, x, nm, nf)
+                assert z.export_tree() == s.export_tree()
+                e, e0 = s.phi(b, excl=excl), z.phi(b)
+                assert abs(e.phi - e0.phi) <= 1e-12 * e0.abs_sum, (excl, e.phi, e0.phi)
+
 def test_tree_matches_brute_force_including_ties(oracle_mod):
     rng = np.random.default_rng(21)
     for C, Dmax in [(2, 6), (3, 8), (8, 20)]:
