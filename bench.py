@@ -93,7 +93,10 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # raw samples: BHMC_CLOCKS_CSV if set, else a file in the temporary directory
+        import tempfile
+        self.path = os.environ.get("BHMC_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "bhmc_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
