@@ -101,70 +101,6 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     b = ld_int4(S.nB + g0 + (tid & 7));
     a = ld_float4(S.nA + g0 + (tid & 7));
   }
-  // The root's children: when each of them is internal with N' > N0 and fails
-  // the MAC for every point by more than the FP32 test's margin, or holds no
-  // charge but the moved ones, their round would only open them all.  Then the
-  // walk starts from their children's groups instead, with the counters, paths
-  // and stack order that round would have left (so the sums are bit-identical).
-  if (skip_root) {
-    const int node = g0 + (tid & 7);
-    const unsigned long long key = ((unsigned long long)(unsigned)b.w << 32) | (unsigned)b.z;
-    unsigned onp = 0;
-    bool ok = true, opened = false;
-    if (g == 0 && key != 0ULL) {
-      const int sh = 3 * (S.Dmax - 1);
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (((pm0 >> s) & 1u) && (unsigned)((T.pkey[s] >> sh) & 7ULL) == (unsigned)(tid & 7)) onp |= 1u << s;
-      const unsigned emask = (onp & 1u) | (T.n_excl > 1 ? ((onp >> 1) & 2u) : 0u);
-      const int np = b.y - __popc(emask);
-      if (np > 0) {
-        const float rho2 = 3.0f * a.w * a.w;
-        const float lo_t = rho2 * 0.9999923706054688f;  // 1 - 2^-17, the traversal's margin
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const float4 h = T.h4[s], l = T.l4[s];
-          const float rx = (a.x - h.x) - l.x, ry = (a.y - h.y) - l.y, rz = (a.z - h.z) - l.z;
-          const float tt = S.theta2f * (rx * rx + ry * ry + rz * rz);
-          if (((pmask >> s) & 1u) && !(tt <= lo_t)) ok = false;
-        }
-        ok = ok && b.x >= 0 && np > S.N0;
-        opened = ok;
-      }
-    }
-    if (__syncthreads_and(ok)) {
-      const unsigned ob = __ballot_sync(FULL, opened);  // warp 0: the opened children, in order
-      if (g == 0 && key != 0ULL) {
-        visited += __popc(pmask);
-        if (path) {
-          unsigned pr = onp & pmask;
-          while (pr) {
-            const int s = __ffs(pr) - 1;
-            pr &= pr - 1;
-            path[s][1] = node;
-            if (b.x < 0) leafcnt[s] = b.y;
-          }
-        }
-        if (opened)
-          B.stk[__popc(ob & lt)] = make_uint2((unsigned)b.x, pmask | (onp << 8) | (2u << 12));
-      }
-      if (tid == 0) B.wcnt[0][0] = __popc(ob);
-      __syncthreads();
-      const int n1 = B.wcnt[0][0];
-      npop = min(n1, G);
-      e = make_uint2(0u, 0u);
-      b = make_int4(-1, 0, 0, 0);
-      a = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (g < npop) {
-        e = B.stk[n1 - 1 - g];
-        const int nn = (int)e.x + (tid & 7);
-        b = ld_int4(S.nB + nn);
-        a = ld_float4(S.nA + nn);
-      }
-      top = n1 - npop;
-      __syncthreads();
-    }
-  }
   // Multipole and direct terms of one round's item lists; the first direct
   // pass's slot loads are issued before the multipole work.
   auto run_items = [&](int tm_, int td_) {
