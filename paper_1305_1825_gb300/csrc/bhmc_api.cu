@@ -1080,8 +1080,11 @@ bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, 
   return radial_impl(B->reps.data(), (int)B->reps.size(), nbins, r_lo, r_hi, counts, charge);
 }
 
-bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
-                               uint64_t move0, bhmc_mc_stats* stats) {
+}  // extern "C"
+
+// Checks of a batched call and the host copy of its arguments (seeds uploaded).
+static bhmc_status batch_prepare(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
+                                 uint64_t move0) {
   if (B)
     for (bhmc_ctx* c : B->reps) c->w_stale = true;
   if (!B || !seeds || !(step >= 0.0)) return BHMC_EINVAL;
@@ -1097,6 +1100,16 @@ bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, con
   B->h_args->step = step;
   B->h_args->seeds = B->d_seeds;
   B->h_args->order = B->d_order;
+  return BHMC_OK;
+}
+
+extern "C" {
+
+bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
+                               uint64_t move0, bhmc_mc_stats* stats) {
+  bhmc_status rc0 = batch_prepare(B, n_moves, step, seeds, move0);
+  if (rc0 != BHMC_OK) return rc0;
+  const int n = (int)B->reps.size();
   CK(cudaGraphLaunch(B->graph, B->stream));
   bhmc_status rc = BHMC_OK;
   for (bhmc_ctx* c : B->reps) {
@@ -1110,21 +1123,10 @@ bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, con
 
 bhmc_status bhmc_batch_step_mc_spec(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
                                     uint64_t move0, int32_t proposals, bhmc_mc_stats* stats) {
-  if (B)
-    for (bhmc_ctx* c : B->reps) c->w_stale = true;
-  if (!B || !seeds || !(step >= 0.0) || proposals < 1 || proposals > BHMC_MAX_PROPOSALS) return BHMC_EINVAL;
+  if (proposals < 1 || proposals > BHMC_MAX_PROPOSALS) return BHMC_EINVAL;
+  bhmc_status rc0 = batch_prepare(B, n_moves, step, seeds, move0);
+  if (rc0 != BHMC_OK) return rc0;
   const int n = (int)B->reps.size();
-  for (bhmc_ctx* c : B->reps) {
-    if (c->sticky) return BHMC_ESTATE;
-    if (n_moves > 0 && c->S.n_mob < 1) return BHMC_EINVAL;
-  }
-  CK(cudaMemcpyAsync(B->d_seeds, seeds, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, B->stream));
-  CK(cudaStreamSynchronize(B->stream));
-  B->h_args->n_moves = n_moves;
-  B->h_args->move0 = move0;
-  B->h_args->step = step;
-  B->h_args->seeds = B->d_seeds;
-  B->h_args->order = B->d_order;
   CK(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BatchArgs), cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemsetAsync(B->d_stats, 0, sizeof(bhmc_mc_stats) * n, B->stream));
   if (n_moves) {
