@@ -379,6 +379,25 @@ def test_mc_chain_keeps_tree_canonical(oracle_mod):
     assert out[0] > 500 and out[3] > 0
 
 
+def test_mc_chain_keeps_fixed_level_tree(oracle_mod):
+    """A Metropolis chain on the fixed-level tree of Sec. 3.2 (hard-core double
+    layer, L_max = 6): after 3000 moves every charge still sits in a depth-L_max
+    leaf, the tree equals the one rebuilt from the particle set, and no pair of
+    ions is closer than the hard-core diameter (Eq. 2.1)."""
+    wl = W.edl_hard(n=300, seed=19, Lmax=6)
+    s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+    recs = s.mc_run(seed=5, n_moves=3000, step=wl["step"])
+    assert s.check() == 0
+    tree = s.export_tree()
+    assert tree == _rebuilt(oracle_mod, s, wl).export_tree()
+    assert all(d == 6 for (d, k), (leaf, c, _) in tree.items() if leaf and c > 0)
+    x = s.charges()[1][:300]
+    d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1) + np.eye(300) * 1e9
+    assert d2.min() > 16.0
+    out = np.bincount(recs["outcome"], minlength=5)
+    assert out[0] > 300 and out[3] > 0
+
+
 def test_relative_error_decreases_with_order(oracle_mod):
     """Eq. (4.1) on a snapshot shaped like the Sec. 4 double layer (counterions of
     valence 2 around a macroion, l_B = 7.14): E falls with p and with theta, and
