@@ -157,6 +157,23 @@ def test_truncation_bound(oracle_mod, theta, p):
             assert e.accepted > 0
 
 
+
+def test_cluster_holding_the_point_is_never_approximated(oracle_mod):
+    """A cluster that contains the evaluation point has |r_A - x| <= rho_A, so it
+    fails the MAC for every theta < 1 (Sec. 3.2).  At theta = 0.99 every accepted
+    cluster must still have gamma = rho_A/|r_A - x| < 1: the truncation bound of
+    Eq. (3.4) stays finite and holds at the charges' own positions."""
+    for wl, s in _systems(oracle_mod, 0.99, 6):
+        s.set_bound(True)
+        q, x = s.charges()
+        for j in range(0, s.n_mobile, 29):
+            excl = [j]
+            if wl["params"]["image"]:
+                excl.append(s.n_mobile + s.n_fixed + j)
+            e = s.phi(x[j], excl=excl)
+            assert e.accepted > 0 and math.isfinite(e.bound) and e.bound >= 0.0
+            assert abs(e.phi - s.phi_direct(x[j], excl=excl)) <= e.bound + 1e-12 * e.abs_sum
+
 def test_high_order_converges_to_direct(oracle_mod):
     for wl, s in _systems(oracle_mod, 0.3, 10):
         q, x = s.charges()
