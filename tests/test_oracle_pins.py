@@ -435,6 +435,20 @@ def test_relative_error_decreases_with_order(oracle_mod):
 
 
 
+
+def test_relative_error_roughly_independent_of_n(oracle_mod):
+    """Sec. 4: the Eq. (4.1) error at p = 2 stays of the same size for N from 100
+    up (double-layer snapshots of 100 to 3200 ions): below 1 % / 0.1 % at
+    theta = 0.5 / 0.3 for every N, within a factor of five across N."""
+    for theta, cap in ((0.5, 0.01), (0.3, 0.001)):
+        errs = []
+        for n in (100, 400, 1600, 3200):
+            wl = W.edl(n=n, seed=14, theta=theta, p=2)
+            s = oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+            vt, vd = s.potentials()
+            errs.append(math.sqrt(((vt - vd) ** 2).sum() / (vd ** 2).sum()))
+        assert max(errs) < cap and max(errs) / min(errs) < 5.0, errs
+
 def test_relative_error_on_equilibrated_hard_core_layer(oracle_mod):
     """Eq. (4.1) over every charge, macroion included, on a snapshot of an
     equilibrated chain of the Sec. 4 double layer with hard cores (Eq. 2.1):
