@@ -45,6 +45,7 @@ class Params(C.Structure):
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
         ("hard_core", C.c_double),
         ("fixed_depth", C.c_int32),
+        ("fixed_direct", C.c_int32),
     ]
 
 
@@ -177,6 +178,7 @@ def make_params(d: dict) -> Params:
     P.image_R, P.image_alpha = (d["image"] if d.get("image") else (0.0, 0.0))
     P.hard_core = d.get("hard_core", 0.0) or 0.0
     P.fixed_depth = 1 if d.get("fixed_depth", False) else 0
+    P.fixed_direct = 1 if d.get("fixed_direct", False) else 0
     return P
 
 

@@ -193,6 +193,10 @@ void or_get_charges(const or_sys* s, double* q, double* xyz) {
 
 static int64_t img_index(const or_sys* s, int64_t i) { return s->n_mob + s->n_fix + i; }
 
+/* With fixed_direct, the fixed charges n_mob .. n_mob + n_fix - 1 are not in the tree. */
+static int is_fixed(const or_sys* s, int64_t j) { return j >= s->n_mob && j < s->n_mob + s->n_fix; }
+static int in_tree(const or_sys* s, int64_t j) { return !(s->P.fixed_direct && is_fixed(s, j)); }
+
 int or_image_of(const or_sys* s, const double r[3], double q, double rim[3], double* qim) {
   double R = s->P.image_R;
   double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
@@ -476,6 +480,7 @@ or_sys* or_create(const or_params* P, int64_t n_mob, int64_t n_fix, const double
   R->h = 0.5 * P->root_side;
   for (int a = 0; a < 3; ++a) R->c[a] = P->root_lo[a] + R->h;
   for (int64_t j = 0; j < s->n_tot; ++j) {
+    if (!in_tree(s, j)) continue;
     *track_node(s, j, 0) = 0;
     *track_slot(s, j, 0) = s->nodes[0].n;
     idx_push(&s->nodes[0], j);
@@ -601,6 +606,18 @@ int or_phi(or_sys* s, const double x[3], int n_excl, const int64_t* excl, or_eva
   v.Mp = Mp;
   v.mono = mono;
   or_visit(s, 0, &v);
+  if (s->P.fixed_direct) {
+    /* the fixed charges outside the tree: exact terms q_f / |r_f - x| */
+    for (int64_t j = s->n_mob; j < s->n_mob + s->n_fix; ++j) {
+      if (excluded(&v, j)) continue;
+      double ex = s->x[3 * j] - x[0];
+      double ey = s->x[3 * j + 1] - x[1];
+      double ez = s->x[3 * j + 2] - x[2];
+      double r = sqrt((ex * ex + ey * ey) + ez * ez);
+      out->phi += s->q[j] / r;
+      out->abs_sum += fabs(s->q[j]) / r;
+    }
+  }
   return OR_OK;
 }
 
@@ -887,24 +904,27 @@ double or_energy_direct(const or_sys* s) {
   return or_direct_energy_raw(s->n_tot, s->q, s->x, s->P.lB);
 }
 
+/* Potential at charge j from all other charges: the treecode for a charge in
+   the tree, the exact sum for a fixed charge outside it (fixed_direct). */
+static double target_phi(or_sys* s, int64_t j) {
+  double x[3] = {s->x[3 * j], s->x[3 * j + 1], s->x[3 * j + 2]};
+  if (!in_tree(s, j)) return or_phi_direct(s, x, 1, &j);
+  or_eval e;
+  or_phi(s, x, 1, &j, &e);
+  return e.phi;
+}
+
 /* E_tree = (1/2) l_B sum_i q_i phi_tree(r_i), each charge excluded from its own sum. */
 double or_energy_tree(or_sys* s) {
   double E = 0.0;
-  for (int64_t j = 0; j < s->n_tot; ++j) {
-    or_eval e;
-    double x[3] = {s->x[3 * j], s->x[3 * j + 1], s->x[3 * j + 2]};
-    or_phi(s, x, 1, &j, &e);
-    E += s->q[j] * e.phi;
-  }
+  for (int64_t j = 0; j < s->n_tot; ++j) E += s->q[j] * target_phi(s, j);
   return 0.5 * s->P.lB * E;
 }
 
 int or_potentials(or_sys* s, double* v_tree, double* v_direct) {
   for (int64_t j = 0; j < s->n_tot; ++j) {
-    or_eval e;
     double x[3] = {s->x[3 * j], s->x[3 * j + 1], s->x[3 * j + 2]};
-    or_phi(s, x, 1, &j, &e);
-    if (v_tree) v_tree[j] = s->P.lB * s->q[j] * e.phi;
+    if (v_tree) v_tree[j] = s->P.lB * s->q[j] * target_phi(s, j);
     if (v_direct) v_direct[j] = s->P.lB * s->q[j] * or_phi_direct(s, x, 1, &j);
   }
   return OR_OK;
@@ -998,7 +1018,7 @@ int or_check(const or_sys* s) {
   int rc = check_rec(s, 0, seen);
   if (!rc)
     for (int64_t j = 0; j < s->n_tot; ++j)
-      if (!seen[j]) {
+      if (seen[j] != in_tree(s, j)) {
         rc = 12;
         break;
       }
@@ -1039,6 +1059,25 @@ typedef struct {
   double tg[3];  /* grad phi_i (target side) */
 } or_adj;
 
+/* One exact pair (target v->target, source j): potential, target gradient and
+   the source side's position and charge derivatives. */
+static void or_adj_pair(or_sys* s, int64_t j, or_adj* v) {
+  int64_t i = v->target;
+  double ex = s->x[3 * j] - v->x[0], ey = s->x[3 * j + 1] - v->x[1], ez = s->x[3 * j + 2] - v->x[2];
+  double r2 = (ex * ex + ey * ey) + ez * ez;
+  double r = sqrt(r2), r3 = r2 * r;
+  v->phi += s->q[j] / r;
+  /* target: d/dx q_j/|r_j - x| = q_j (r_j - x)/r^3 */
+  v->tg[0] += s->q[j] * ex / r3;
+  v->tg[1] += s->q[j] * ey / r3;
+  v->tg[2] += s->q[j] * ez / r3;
+  /* source: q_i q_j d/dr_j 1/|r_j - r_i| = -q_i q_j (r_j - r_i)/r^3 */
+  v->src[3 * j + 0] -= s->q[i] * s->q[j] * ex / r3;
+  v->src[3 * j + 1] -= s->q[i] * s->q[j] * ey / r3;
+  v->src[3 * j + 2] -= s->q[i] * s->q[j] * ez / r3;
+  v->dq[j] += s->q[i] / r;
+}
+
 static void or_adj_visit(or_sys* s, int a, or_adj* v) {
   or_node* A = &s->nodes[a];
   int64_t i = v->target;
@@ -1074,19 +1113,7 @@ static void or_adj_visit(or_sys* s, int a, or_adj* v) {
   for (int64_t k = 0; k < A->n; ++k) {
     int64_t j = A->idx[k];
     if (j == i) continue;
-    double ex = s->x[3 * j] - v->x[0], ey = s->x[3 * j + 1] - v->x[1], ez = s->x[3 * j + 2] - v->x[2];
-    double r2 = (ex * ex + ey * ey) + ez * ez;
-    double r = sqrt(r2), r3 = r2 * r;
-    v->phi += s->q[j] / r;
-    /* target: d/dx q_j/|r_j - x| = q_j (r_j - x)/r^3 */
-    v->tg[0] += s->q[j] * ex / r3;
-    v->tg[1] += s->q[j] * ey / r3;
-    v->tg[2] += s->q[j] * ez / r3;
-    /* source: q_i q_j d/dr_j 1/|r_j - r_i| = -q_i q_j (r_j - r_i)/r^3 */
-    v->src[3 * j + 0] -= s->q[i] * s->q[j] * ex / r3;
-    v->src[3 * j + 1] -= s->q[i] * s->q[j] * ey / r3;
-    v->src[3 * j + 2] -= s->q[i] * s->q[j] * ez / r3;
-    v->dq[j] += s->q[i] / r;
+    or_adj_pair(s, j, v);
   }
 }
 
@@ -1107,7 +1134,16 @@ int or_forces(or_sys* s, double* dEdr, double* dEdq) {
       v.tg[c] = 0.0;
     }
     v.phi = 0.0;
-    or_adj_visit(s, 0, &v);
+    if (in_tree(s, i)) {
+      or_adj_visit(s, 0, &v);
+      /* fixed_direct: the fixed charges outside the tree, exact pairs */
+      if (s->P.fixed_direct)
+        for (int64_t j = s->n_mob; j < s->n_mob + s->n_fix; ++j) or_adj_pair(s, j, &v);
+    } else {
+      /* a fixed charge outside the tree: exact pairs with every other charge */
+      for (int64_t j = 0; j < s->n_tot; ++j)
+        if (j != i) or_adj_pair(s, j, &v);
+    }
     phi[i] = v.phi;
     for (int c = 0; c < 3; ++c) tgt[3 * i + c] = s->q[i] * v.tg[c];
   }
@@ -1225,6 +1261,18 @@ int or_phi_grad(or_sys* s, const double x[3], int n_excl, const int64_t* excl, d
   double T1[286], Mp[286], mono[286];
   or_grad_ctx v = {x, n_excl, excl, 0.0, {0.0, 0.0, 0.0}, T1, Mp, mono};
   or_grad_visit(s, 0, &v);
+  if (s->P.fixed_direct) {
+    /* the fixed charges outside the tree: exact terms and their gradients */
+    for (int64_t j = s->n_mob; j < s->n_mob + s->n_fix; ++j) {
+      if (excl_has(&v, j)) continue;
+      double ex = s->x[3 * j] - x[0], ey = s->x[3 * j + 1] - x[1], ez = s->x[3 * j + 2] - x[2];
+      double r2 = (ex * ex + ey * ey) + ez * ez, r = sqrt(r2), r3 = r2 * r;
+      v.phi += s->q[j] / r;
+      v.g[0] += s->q[j] * ex / r3;
+      v.g[1] += s->q[j] * ey / r3;
+      v.g[2] += s->q[j] * ez / r3;
+    }
+  }
   *phi = v.phi;
   g[0] = v.g[0];
   g[1] = v.g[1];

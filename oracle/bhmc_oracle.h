@@ -60,6 +60,10 @@ typedef struct {
   double hard_core; /* common diameter tau of the mobile ions (Eq. 2.1), 0: none */
   int32_t fixed_depth; /* 1: the Sec. 3.2 tree of fixed level L_max = Dmax: every
                           non-empty cluster above Dmax splits, leaves are at Dmax */
+  int32_t fixed_direct; /* 1: the fixed charges (the macroion of Sec. 4, fixed at the
+                           cell centre) stay out of the tree; every potential adds their
+                           exact terms q_f / |x - r_f|, and the potential at a fixed
+                           charge is the exact sum over all other charges */
 } or_params;
 
 typedef struct or_sys or_sys;
@@ -114,7 +118,9 @@ int64_t or_n_charges(const or_sys* s);
 void or_get_charges(const or_sys* s, double* q, double* xyz);
 int or_image_of(const or_sys* s, const double r[3], double q, double rim[3], double* qim);
 
-/* Potential at x from all charges except the n_excl listed ones (pre-move tree). */
+/* Potential at x from all charges except the n_excl listed ones (pre-move tree);
+   with fixed_direct the fixed charges enter as exact terms (counted in abs_sum,
+   not in the interaction-list counters). */
 int or_phi(or_sys* s, const double x[3], int n_excl, const int64_t* excl, or_eval* out);
 double or_phi_direct(const or_sys* s, const double x[3], int n_excl, const int64_t* excl);
 
@@ -133,7 +139,8 @@ int or_mc_run(or_sys* s, uint64_t seed, uint32_t replica, uint64_t m0, int64_t n
 /* Total energies over all charges (ions, fixed charges, images). */
 double or_energy_direct(const or_sys* s);
 double or_energy_tree(or_sys* s);
-/* V-bar_i = l_B q_i phi_tree(r_i) and V_i = l_B q_i phi_direct(r_i) for every charge (Eq. 4.1). */
+/* V-bar_i = l_B q_i phi_tree(r_i) and V_i = l_B q_i phi_direct(r_i) for every charge (Eq. 4.1);
+   with fixed_direct the potential at a fixed charge is exact on both sides. */
 int or_potentials(or_sys* s, double* v_tree, double* v_direct);
 
 /* Exact gradient of the total treecode energy with every MAC decision held

@@ -14,7 +14,10 @@ Workloads (all lengths in the same unit as the Bjerrum length l_B):
   directions uniform; ions confined to R + 0.5 <= |r| <= r_max; each ion carries
   a point image (position R^2 r/|r|^2, charge -0.3 q R/|r|).  This mirrors the
   electric double layer around a spherical macroion of Sec. 4 of the paper
-  (which uses counterions only, a hard-core diameter and l_B = 7.14).
+  (which uses counterions only, a hard-core diameter and l_B = 7.14).  The
+  macroion is fixed at the centre and, by default (``fixed_direct``), held
+  outside the tree: the tree holds the 2N ions and images, and the macroion's
+  interactions are exact.
 * ``batch``   -- replicas of ``colloid`` with N drawn uniformly from
   [2000, 50000] (N - |Z| even).
 * ``uniform`` -- N charges of alternating sign uniform in [-50, 50)^3.
@@ -69,7 +72,7 @@ def root_for(rmax: float) -> tuple:
 
 def colloid(n: int = 10000, seed: int = 2, R: float = 10.0, Z: float = -60.0,
             rmax: float = 50.0, theta: float = 0.5, p: int = 4, C: int = 8,
-            Dmax: int = 20) -> dict:
+            Dmax: int = 20, fixed_direct: bool = True) -> dict:
     rng = np.random.default_rng(seed)
     nz = int(round(abs(Z)))
     if n < nz or (n - nz) % 2:
@@ -86,7 +89,7 @@ def colloid(n: int = 10000, seed: int = 2, R: float = 10.0, Z: float = -60.0,
     rng.shuffle(q)
     lo, side = root_for(rmax)
     params = base_params(theta=theta, p=p, C=C, Dmax=Dmax, root_lo=lo, root_side=side,
-                         shell=(rmin, rmax), image=(R, -0.3))
+                         shell=(rmin, rmax), image=(R, -0.3), fixed_direct=fixed_direct)
     q_all = np.concatenate([q, [Z]])
     xyz_all = np.concatenate([xyz, np.zeros((1, 3))], axis=0)
     return dict(name="colloid-N%d" % n, params=params, q=q_all, xyz=xyz_all, n_mobile=n,
@@ -102,9 +105,10 @@ def batch_sizes(n_rep: int = 256, seed: int = 3, lo: int = 2000, hi: int = 50000
 
 
 def batch(n_rep: int = 256, seed: int = 3, theta: float = 0.5, p: int = 4, C: int = 8,
-          sizes=None) -> list:
+          sizes=None, fixed_direct: bool = True) -> list:
     sizes = sizes if sizes is not None else batch_sizes(n_rep, seed)
-    return [colloid(n=sizes[r], seed=1000 + r, theta=theta, p=p, C=C) for r in range(len(sizes))]
+    return [colloid(n=sizes[r], seed=1000 + r, theta=theta, p=p, C=C, fixed_direct=fixed_direct)
+            for r in range(len(sizes))]
 
 
 def uniform(n: int = 100000, seed: int = 4, theta: float = 0.5, p: int = 4, C: int = 8) -> dict:
@@ -116,11 +120,12 @@ def uniform(n: int = 100000, seed: int = 4, theta: float = 0.5, p: int = 4, C: i
                 step=1.0, seed=seed)
 
 
-def large(n: int = 1000000, seed: int = 5, theta: float = 0.5, p: int = 6) -> dict:
-    return colloid(n=n, seed=seed, R=40.0, Z=-2000.0, rmax=400.0, theta=theta, p=p)
+def large(n: int = 1000000, seed: int = 5, theta: float = 0.5, p: int = 6, fixed_direct: bool = True) -> dict:
+    return colloid(n=n, seed=seed, R=40.0, Z=-2000.0, rmax=400.0, theta=theta, p=p, fixed_direct=fixed_direct)
 
 
-def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8) -> dict:
+def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8,
+        fixed_direct: bool = True) -> dict:
     """Snapshot shaped like the electric double layer of Sec. 4: n counterions of
     valence 2 around a fixed macroion of radius 30 and valence -2n, cell radius
     80, l_B = 7.14, radii drawn from exp(-(r - 30)/2) + 0.05 on [32, 78].  The
@@ -131,7 +136,7 @@ def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8)
     xyz = r[:, None] * _unit_vectors(rng, n)
     lo, side = root_for(rcell)
     params = base_params(lB=7.14, theta=theta, p=p, C=C, root_lo=lo, root_side=side,
-                         shell=(a + tau / 2, rcell - tau / 2))
+                         shell=(a + tau / 2, rcell - tau / 2), fixed_direct=fixed_direct)
     q = np.concatenate([np.full(n, 2.0), [-2.0 * n]])
     xyz = np.concatenate([xyz, np.zeros((1, 3))], axis=0)
     return dict(name="edl-N%d" % n, params=params, q=q, xyz=xyz, n_mobile=n, n_fixed=1,
@@ -139,7 +144,7 @@ def edl(n: int = 800, seed: int = 6, theta: float = 0.5, p: int = 2, C: int = 8)
 
 
 def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int = 8,
-             Lmax: int = 0) -> dict:
+             Lmax: int = 0, fixed_direct: bool = True) -> dict:
     """The electric double layer of Sec. 4 with its hard cores (Eq. 2.1): n
     counterions of valence 2 and diameter 4 around a fixed macroion of radius
     30 and valence -2n in a cell of radius 80, l_B = 7.14.  Ion centres lie in
@@ -166,7 +171,7 @@ def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int
         cells.setdefault(c, []).append(k)
     lo, side = root_for(rcell)
     params = base_params(lB=7.14, theta=theta, p=p, C=C, root_lo=lo, root_side=side,
-                         shell=(rmin, rmax), hard_core=tau)
+                         shell=(rmin, rmax), hard_core=tau, fixed_direct=fixed_direct)
     if Lmax > 0:
         params.update(Dmax=Lmax, fixed_depth=True)
     q = np.concatenate([np.full(n, 2.0), [-2.0 * n]])
@@ -175,7 +180,8 @@ def edl_hard(n: int = 800, seed: int = 8, theta: float = 0.5, p: int = 2, C: int
                 step=2.0, seed=seed)
 
 
-def colloid_scaled(n: int = 100000, seed: int = 7, theta: float = 0.5, p: int = 4) -> dict:
+def colloid_scaled(n: int = 100000, seed: int = 7, theta: float = 0.5, p: int = 4,
+                   fixed_direct: bool = True) -> dict:
     """The colloid radial law scaled to n ions: lengths R and r_max times
     s = (n / 1e4)^(1/3), macroion charge Z times s^2 (nearest value with n - |Z|
     even), decay length 2 kept."""
@@ -183,4 +189,5 @@ def colloid_scaled(n: int = 100000, seed: int = 7, theta: float = 0.5, p: int = 
     nz = int(round(60 * s * s))
     if (n - nz) % 2:
         nz += 1
-    return colloid(n=n, seed=seed, R=10.0 * s, Z=-float(nz), rmax=50.0 * s, theta=theta, p=p)
+    return colloid(n=n, seed=seed, R=10.0 * s, Z=-float(nz), rmax=50.0 * s, theta=theta, p=p,
+                   fixed_direct=fixed_direct)
