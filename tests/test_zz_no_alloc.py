@@ -1,15 +1,16 @@
 """The allocation-free direct-sum energy entry point, called through the C-ABI.
 
-bhmc_energy_direct_noalloc serves callers that cannot allocate device memory
-when they need the energy (inside stream capture, from host functions on a
-stream, or when the host owns the device-memory budget).  It must agree with
-bhmc_energy_direct, whose scratch comes from cudaMalloc, on two calls in a row
-(the second call reuses the fixed scratch left by the first).  This file is
-named so that pytest collects it last.
+bhmc_energy_direct_noalloc serves callers that cannot call cudaMalloc when they
+need the energy: applications that reserve their device memory up front and
+hand libraries only pre-allocated buffers, and loops that must not take the
+device-wide synchronisation an allocation can cause.  It must agree with
+bhmc_energy_direct, whose scratch comes from cudaMalloc, and with the FP64 CPU
+oracle's direct sum, on two calls in a row (the second call reuses the fixed
+scratch left by the first).  This file is named so that pytest collects it
+last.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from paper_1305_1825_gb300 import workloads as W
@@ -23,6 +24,7 @@ def test_noalloc_direct_energy_matches_allocating_call():
         pytest.skip("no CUDA device")
     import __graft_entry__
     __graft_entry__.build()
+    import oracle
     from paper_1305_1825_gb300 import bhmc
     lib = bhmc.lib()
     lib.bhmc_energy_direct_noalloc.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -32,6 +34,8 @@ def test_noalloc_direct_energy_matches_allocating_call():
         ctx = bhmc.Context(wl)
         ref = ctx.energy_direct()
         q, x = ctx.charges()
+        # the oracle's O(N^2) sum of Eq. (1.1) over the same charges (FP64, CPU)
+        ref_or = oracle.direct_energy_raw(q, x, wl["params"]["lB"])
         qd = torch.tensor(q, dtype=torch.float64, device="cuda")
         xd = torch.tensor(x.reshape(-1), dtype=torch.float64, device="cuda")
         for _ in range(2):
@@ -42,8 +46,9 @@ def test_noalloc_direct_energy_matches_allocating_call():
             torch.cuda.synchronize()
             # same FP64 pair sums, partials added in a different order
             assert E.item() == pytest.approx(ref, rel=1e-9)
+            assert E.item() == pytest.approx(ref_or, rel=1e-9)
         ctx.close()
     # sizes beyond the fixed scratch are refused before any launch
     rc = lib.bhmc_energy_direct_noalloc(1048577, qd.data_ptr(), xd.data_ptr(), 1.0, E.data_ptr(),
                                         stream.cuda_stream)
-    assert rc == 11
+    assert rc == bhmc.ESCRATCH
