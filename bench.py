@@ -166,7 +166,8 @@ def workload(args, rank=0):
 
 def config(args, sizes, extra=None):
     c = {"workload": "colloid-%d-replicas" % args.reps, "replicas": args.reps,
-         "N_range": [min(sizes), max(sizes)], "charges_per_replica": "2N+1 (ions, images, macroion)",
+         "N_range": [min(sizes), max(sizes)],
+         "charges_per_replica": "2N in the tree (ions and images) + the macroion, whose interactions are exact",
          "moves_per_replica_per_step": args.moves, "theta": args.theta, "p": args.p, "C": args.C,
          "warps_per_move": args.warps, "layout": args.layout, "step": 1.0,
          "l2": "inputs larger than L2: the replicas' trees total several GB"}
@@ -191,32 +192,69 @@ def oracle_sample(systems, seeds, moves, budget_s):
     return done / t_total, "%d replicas x %d moves (FP64 oracle treecode chain, single thread)" % (used, moves)
 
 
+def _oracle_worker(task):
+    """One host core: the FP64 oracle chains of a list of replicas; returns
+    (moves, seconds spent in the chains)."""
+    import oracle
+    work, moves = task
+    done, t_total = 0, 0.0
+    for (r, seed, wl) in work:
+        ref = oracle.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
+        t = time.perf_counter()
+        ref.mc_run(seed, moves, replica=r)
+        t_total += time.perf_counter() - t
+        done += moves
+    return done, t_total
+
+
+def oracle_sample_parallel(systems, seeds, moves, per_core):
+    """The oracle's replica chains spread over every host core (a spawned
+    process per core, `per_core` replicas each); moves/s = all moves over the
+    busiest core's chain time.  Returns (moves/s, cores, sample text)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = min(len(systems), cores * per_core)
+    tasks = [([(r, seeds[r], systems[r]) for r in range(c, n, cores)], moves) for c in range(cores)]
+    tasks = [t for t in tasks if t[0]]
+    with mp.get_context("spawn").Pool(len(tasks)) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    total = sum(m for m, _ in res)
+    busiest = max(t for _, t in res)
+    return total / busiest, len(tasks), ("%d replicas x %d moves over %d host processes (FP64 oracle treecode "
+                                         "chains, replica-parallel)" % (n, moves, len(tasks)))
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
     sizes, systems, seeds = workload(args)
     vals = []
-    sample = ""
+    sample, cores = "", 1
     for s in range(args.warmup + args.steps):
-        v, sample = oracle_sample(systems, seeds, 400, 3.0)
+        v, cores, sample = oracle_sample_parallel(systems, seeds, 150, 1)
         if s >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config(args, sizes),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": config(args, sizes, {"parallelism": "replicas" if args.gpus == 1 else
+                                          "replicas x %d ranks" % args.gpus}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def algorithmic_bytes_per_move(bh, batch, systems, K, acc_rate, n_sample_reps=8, n_moves=24):
-    """Average algorithmic bytes of one trial move from the interaction-list
-    counters (equal to the oracle's): 32 B per visited (cluster, point) header,
-    4K B of FP32 moments per multipole evaluation, 32 B per direct pair, and on
-    acceptance (20K + 32) B per cluster on the four ancestor paths."""
+    """Algorithmic bytes of one trial move from the interaction-list counters
+    (equal to the oracle's): 16 B per visited (cluster, point) pair, 4K B of
+    moments per multipole evaluation, 16 B per direct pair, and on acceptance
+    2 d K 16 B (FP64 moments read and written) + 8 K d B (FP32 mirror) on the
+    path of each moved charge (the ion and its image; d = mean leaf depth).
+    `layout` counts the bytes of this build's records instead: 32 B cluster
+    headers, 32 B leaf slots and (20K + 32) B per cluster on the four ancestor
+    paths of an accepted move."""
     import numpy as np
     rng = np.random.default_rng(0)
     V = A = Pp = 0
@@ -243,11 +281,38 @@ def algorithmic_bytes_per_move(bh, batch, systems, K, acc_rate, n_sample_reps=8,
                 depth_n += cnt_
     V, A, Pp = V / n, A / n, Pp / n
     depth = depth_sum / max(depth_n, 1)
-    commit = acc_rate * 4 * (depth + 1) * (20 * K + 32)
-    b = 32 * V + 4 * K * A + 32 * Pp + commit
+    moved = 2 if systems[0]["params"].get("image") else 1
+    commit = acc_rate * moved * (2 * depth * K * 16 + 8 * K * depth)
+    b = 16 * V + 4 * K * A + 16 * Pp + commit
+    layout = 32 * V + 4 * K * A + 32 * Pp + acc_rate * 4 * (depth + 1) * (20 * K + 32)
     flops = A * (10 * K) + Pp * 14
     return b, {"visited": V, "multipole": A, "direct_pairs": Pp, "leaf_depth": depth,
-               "commit_bytes": commit, "fp32_flops": flops}
+               "moved_charges": moved, "commit_bytes": commit, "layout_bytes": layout, "fp32_flops": flops}
+
+
+def de_error_sample(bh, wl, n, seed, warps, layout):
+    """dE of the FP32 traversal against the FP64 traversal at the same theta and
+    p (the FP64 mode equals the FP64 oracle within 1e-12 of the interaction
+    sums, a parity-tested bar) on n random moves of one replica."""
+    import numpy as np
+    c32 = bh.Context(wl, warps=warps, layout=layout)
+    c64 = bh.Context(wl, precision=bh.PREC_F64, warps=warps)
+    rng = np.random.default_rng(seed)
+    rel = []
+    for _ in range(n):
+        i = int(rng.integers(0, wl["n_mobile"]))
+        b = wl["xyz"][i] + rng.uniform(-0.5, 0.5, 3)
+        rc, d32, _ = c32.delta_energy(i, b)
+        rc2, d64, _ = c64.delta_energy(i, b)
+        if rc or rc2:
+            continue
+        rel.append(abs(d32 - d64) / max(abs(d64), 1e-300))
+    c32.close()
+    c64.close()
+    rel = np.array(rel)
+    return {"vs": "FP64 traversal (= FP64 oracle within 1e-12 of the interaction sums, tested)",
+            "samples": int(len(rel)), "median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
+            "max": float(rel.max())}
 
 
 def plain_rate(bh, wl, warps, moves=400):
@@ -329,25 +394,32 @@ def run_gpu(args):
     pk, pk_src = peaks()
     bpm, detail = algorithmic_bytes_per_move(bhmc, batch, systems, K, acc_rate)
     launch_ms = ms / args.steps
-    achieved = bpm * args.reps * args.moves / (launch_ms / 1e3) / 1e9
+    moves_per_launch = args.reps * args.moves
+    achieved = bpm * moves_per_launch / (launch_ms / 1e3) / 1e9
     trec = traffic_record()
-    traffic = trec["dram_bytes_per_move"] * args.reps * args.moves if trec else None
+    traffic = trec["dram_bytes_per_move"] * moves_per_launch if trec else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "peak_source": pk_src,
             "traffic_note": ("ncu dram bytes per move of a 96-replica capture x moves per launch"
                              if trec else "kernel changed since the last ncu capture"),
             "kernel": "k_batch (persistent, one replica per block)",
-            "bytes_per_move": bpm, "per_move": detail}
+            "bytes_per_move": bpm, "bytes_per_move_layout": detail["layout_bytes"],
+            "frac_layout_bytes": detail["layout_bytes"] * moves_per_launch / (launch_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+            "dram_frac": (traffic / (launch_ms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None,
+            "per_move": detail}
     extra = {}
     if not args.no_plain:
         wl1 = W.colloid(n=10000, seed=2, theta=args.theta, p=args.p, C=args.C)
         pr = plain_rate(bhmc, wl1, args.warps)
         extra = {"plain_moves_per_s_colloid_N1e4": pr, "batched_per_replica_moves_per_s": value / args.reps / world,
                  "batched_over_plain": value / pr, "acceptance": acc_rate}
+    extra["dE_error"] = de_error_sample(bhmc, systems[0], 200, 17, args.warps, layout)
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        v, sample = oracle_sample(systems, seeds, 500, 15.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        v1, sample1 = oracle_sample(systems, seeds, 300, 5.0)
+        v, cores, sample = oracle_sample_parallel(systems, seeds, 300, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": v1, "cores": 1, "sample": sample1}}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -488,7 +560,10 @@ def _field_item(bh, name, wl, reps=3):
     ms_e = min(_ev_time(ctx.energy)[0] for _ in range(reps))
     p = wl["params"]["p"]
     K = (p + 1) * (p + 2) * (p + 3) // 6
-    bytes_e = 32 * cnt.visited + 4 * K * cnt.accepted + 32 * cnt.pairs
+    # algorithmic bytes (16 B per visited cluster and per direct pair, 4K B per
+    # multipole evaluation) and this build's record bytes (32 B headers and slots)
+    bytes_e = 16 * cnt.visited + 4 * K * cnt.accepted + 16 * cnt.pairs
+    bytes_layout = 32 * cnt.visited + 4 * K * cnt.accepted + 32 * cnt.pairs
     pk, pk_src = peaks()
     dEdr = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
     dEdq = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -504,6 +579,7 @@ def _field_item(bh, name, wl, reps=3):
             "energy_roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                 "frac": achieved / pk["hbm_gbs"], "peak_source": pk_src,
                                 "bytes_per_target": bytes_e / len(q),
+                                "frac_layout_bytes": bytes_layout / (ms_e / 1e3) / 1e9 / pk["hbm_gbs"],
                                 "per_target": {"visited": cnt.visited / len(q), "multipole": cnt.accepted / len(q),
                                                "direct_pairs": cnt.pairs / len(q)}},
             "forces_ms": ms_f, "forces_targets_per_s": len(q) / (ms_f / 1e3),

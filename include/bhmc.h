@@ -89,6 +89,17 @@ typedef struct {
   int32_t fixed_depth; /* 1: the fixed-level tree of Sec. 3.2 with L_max = Dmax (every non-empty
                           cluster above Dmax is bisected, so all charges sit in depth-Dmax
                           leaves); 0: the adaptive tree of leaf capacity C */
+  int32_t fixed_direct; /* 1: the fixed charges (Sec. 4: the macroion, fixed at the cell centre)
+                           stay out of the tree and interact exactly: every potential evaluated
+                           by the treecode adds their terms q_f / |x - r_f| in FP64, and the
+                           potential at a fixed charge is the exact sum over all other charges.
+                           0: fixed charges are ordinary tree charges */
+  int32_t round_limit;  /* iteration budget of the bounded device loops (traversal rounds of a
+                           trial move, stack pops of one warp in the energy and force passes);
+                           0 selects the defaults (2^22 and 2^24).  A loop that runs out stops
+                           and its call returns BHMC_ETIMEOUT; inside a chain (step calls) the
+                           error is also latched, and later calls return BHMC_ESTATE.  A small
+                           value exercises that path without any device fault */
 } bhmc_params;
 
 typedef struct bhmc_ctx bhmc_ctx;
@@ -234,17 +245,22 @@ bhmc_status bhmc_export_tree(bhmc_ctx* ctx, int64_t* rows, int64_t max_rows, int
                              int64_t max_members, double* moments, int64_t* n_rows);
 
 /* Direct-sum total energy E = (1/2) l_B sum_{i != j} q_i q_j / r_ij (FP64) of
-   n charges, for callers that must not allocate device memory: code running
-   during stream capture, host functions enqueued on a stream, or hosts that
-   own all device memory.  The paper has no counterpart; it is the variant of
-   bhmc_energy_direct whose scratch is a fixed 32 KiB array inside the library.
-   q[n], xyz[3n] (x,y,z interleaved) and E[1] are DEVICE pointers; E is written
-   on cuda_stream (no host synchronisation).  n <= 1048576, else BHMC_ESCRATCH.
-   No allocation of any kind happens.  The first call on a device looks up the
-   scratch's device address for that device; make it before capturing a stream.
-   All calls share the scratch, so calls whose kernels overlap on one device
-   race; each call writes every scratch entry it reads, so nothing needs
-   clearing between calls. */
+   n charges, for callers that cannot call cudaMalloc when they need it:
+   applications that reserve their device memory up front and give libraries
+   only pre-allocated buffers, and loops that must not take the device-wide
+   synchronisation an allocation can cause.  The paper has no counterpart; it
+   is the variant of bhmc_energy_direct whose scratch is a fixed 32 KiB
+   __device__ array inside the library (held by every device that loads the
+   library until the process exits).  q[n], xyz[3n] (x,y,z interleaved) and
+   E[1] are DEVICE pointers owned by the caller; E is written on cuda_stream
+   (no host synchronisation).  n <= 1048576, else BHMC_ESCRATCH before any
+   launch; n < 1 or a null pointer: BHMC_EINVAL.  The call allocates nothing
+   (no cudaMalloc, cudaFree or allocating library routine).  The first call in
+   a CUDA context (per device, and again after a device reset) looks up the
+   scratch's device address with that context current; make that first call
+   before any stream capture.  All calls share the scratch, so calls whose
+   kernels overlap on one device race on it; each call writes every scratch
+   entry it reads, so nothing needs clearing between calls. */
 bhmc_status bhmc_energy_direct_noalloc(int64_t n, const double* q, const double* xyz, double lB,
                                        double* E, void* cuda_stream);
 
@@ -268,6 +284,14 @@ bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, 
    (m, r, tag).  stats: n_rep entries (may be NULL). */
 bhmc_status bhmc_batch_step_mc(bhmc_batch* batch, uint64_t n_moves, double step,
                                const uint64_t* seeds, uint64_t move0, bhmc_mc_stats* stats);
+
+/* bhmc_batch_step_mc with one record per trial move: records[r * n_moves + t]
+   (host, n_rep x n_moves, replica-major) receives move t of replica r (the
+   same fields as bhmc_step_mc's records).  The records buffer is allocated on
+   the device for the call.  EINVAL if records is NULL. */
+bhmc_status bhmc_batch_step_mc_records(bhmc_batch* batch, uint64_t n_moves, double step,
+                                       const uint64_t* seeds, uint64_t move0, bhmc_mc_stats* stats,
+                                       bhmc_move_record* records);
 
 /* The same chains as bhmc_batch_step_mc, each on its own thread-block cluster
    of `proposals` CTAs evaluating that many trials per step (as

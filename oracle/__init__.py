@@ -112,6 +112,7 @@ def lib():
         L.or_energy_tree.restype = C.c_double
         L.or_potentials.argtypes = [C.c_void_p, _dp, _dp]
         L.or_forces.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_forces_abs.argtypes = [C.c_void_p, _dp, _dp]
         L.or_ion_energy_grad.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, _dp]
         L.or_phi_grad.argtypes = [C.c_void_p, _dp, C.c_int, _i64p, _dp, _dp]
         L.or_mala_run.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64,
@@ -302,6 +303,16 @@ class System:
         rc = lib().or_forces(self._h, g.ctypes.data_as(_dp), dq.ctypes.data_as(_dp))
         if rc:
             raise ValueError("or_forces failed with status %d" % rc)
+        return g, dq
+
+    def forces_abs(self):
+        """Conditioning sums (A_r (n x 3), A_q (n)): the adjoint with every term
+        replaced by its magnitude."""
+        g = np.zeros((self.n_charges, 3))
+        dq = np.zeros(self.n_charges)
+        rc = lib().or_forces_abs(self._h, g.ctypes.data_as(_dp), dq.ctypes.data_as(_dp))
+        if rc:
+            raise ValueError("or_forces_abs failed with status %d" % rc)
         return g, dq
 
     def export_tree(self):

@@ -1057,7 +1057,11 @@ typedef struct {
   double x[3];
   double phi;    /* phi_i */
   double tg[3];  /* grad phi_i (target side) */
+  int absm;      /* 1: accumulate |term| instead of term (conditioning sums) */
 } or_adj;
+
+/* A term as accumulated: itself, or its magnitude in the conditioning mode. */
+static double adj_term(const or_adj* v, double t) { return v->absm ? fabs(t) : t; }
 
 /* One exact pair (target v->target, source j): potential, target gradient and
    the source side's position and charge derivatives. */
@@ -1066,16 +1070,16 @@ static void or_adj_pair(or_sys* s, int64_t j, or_adj* v) {
   double ex = s->x[3 * j] - v->x[0], ey = s->x[3 * j + 1] - v->x[1], ez = s->x[3 * j + 2] - v->x[2];
   double r2 = (ex * ex + ey * ey) + ez * ez;
   double r = sqrt(r2), r3 = r2 * r;
-  v->phi += s->q[j] / r;
+  v->phi += adj_term(v, s->q[j] / r);
   /* target: d/dx q_j/|r_j - x| = q_j (r_j - x)/r^3 */
-  v->tg[0] += s->q[j] * ex / r3;
-  v->tg[1] += s->q[j] * ey / r3;
-  v->tg[2] += s->q[j] * ez / r3;
+  v->tg[0] += adj_term(v, s->q[j] * ex / r3);
+  v->tg[1] += adj_term(v, s->q[j] * ey / r3);
+  v->tg[2] += adj_term(v, s->q[j] * ez / r3);
   /* source: q_i q_j d/dr_j 1/|r_j - r_i| = -q_i q_j (r_j - r_i)/r^3 */
-  v->src[3 * j + 0] -= s->q[i] * s->q[j] * ex / r3;
-  v->src[3 * j + 1] -= s->q[i] * s->q[j] * ey / r3;
-  v->src[3 * j + 2] -= s->q[i] * s->q[j] * ez / r3;
-  v->dq[j] += s->q[i] / r;
+  v->src[3 * j + 0] += adj_term(v, -(s->q[i] * s->q[j] * ex / r3));
+  v->src[3 * j + 1] += adj_term(v, -(s->q[i] * s->q[j] * ey / r3));
+  v->src[3 * j + 2] += adj_term(v, -(s->q[i] * s->q[j] * ez / r3));
+  v->dq[j] += adj_term(v, s->q[i] / r);
 }
 
 static void or_adj_visit(or_sys* s, int a, or_adj* v) {
@@ -1098,11 +1102,11 @@ static void or_adj_visit(or_sys* s, int a, or_adj* v) {
           int n3 = k - n1 - n2;
           int t = or_term_index(n1, n2, n3);
           double Tn = v->T1[t], Mn = A->M[t];
-          v->phi += Tn * Mn;
-          v->tg[0] -= (n1 + 1) * v->T1[or_term_index(n1 + 1, n2, n3)] * Mn;
-          v->tg[1] -= (n2 + 1) * v->T1[or_term_index(n1, n2 + 1, n3)] * Mn;
-          v->tg[2] -= (n3 + 1) * v->T1[or_term_index(n1, n2, n3 + 1)] * Mn;
-          v->lam[(int64_t)a * K + t] += s->q[i] * Tn;
+          v->phi += adj_term(v, Tn * Mn);
+          v->tg[0] += adj_term(v, -((n1 + 1) * v->T1[or_term_index(n1 + 1, n2, n3)] * Mn));
+          v->tg[1] += adj_term(v, -((n2 + 1) * v->T1[or_term_index(n1, n2 + 1, n3)] * Mn));
+          v->tg[2] += adj_term(v, -((n3 + 1) * v->T1[or_term_index(n1, n2, n3 + 1)] * Mn));
+          v->lam[(int64_t)a * K + t] += adj_term(v, s->q[i] * Tn);
         }
     return;
   }
@@ -1117,10 +1121,11 @@ static void or_adj_visit(or_sys* s, int a, or_adj* v) {
   }
 }
 
-int or_forces(or_sys* s, double* dEdr, double* dEdq) {
+static int or_forces_impl(or_sys* s, double* dEdr, double* dEdq, int absm) {
   int K = s->K, p = s->P.p;
   if (p + 1 > OR_PMAX) return OR_EINVAL; /* orders up to p + 1 enter the target gradient */
   or_adj v;
+  v.absm = absm;
   v.lam = (double*)calloc((size_t)s->n_nodes * K, sizeof(double));
   v.src = (double*)calloc((size_t)s->n_tot * 3, sizeof(double));
   v.dq = (double*)calloc((size_t)s->n_tot, sizeof(double));
@@ -1145,7 +1150,7 @@ int or_forces(or_sys* s, double* dEdr, double* dEdq) {
         if (j != i) or_adj_pair(s, j, &v);
     }
     phi[i] = v.phi;
-    for (int c = 0; c < 3; ++c) tgt[3 * i + c] = s->q[i] * v.tg[c];
+    for (int c = 0; c < 3; ++c) tgt[3 * i + c] = adj_term(&v, s->q[i]) * v.tg[c];
   }
   /* cluster adjoints back to their members: every cluster containing charge k */
   for (int64_t k = 0; k < s->n_tot; ++k) {
@@ -1167,16 +1172,17 @@ int or_forces(or_sys* s, double* dEdr, double* dEdq) {
           for (int n2 = kk - n1; n2 >= 0; --n2) {
             int n3 = kk - n1 - n2;
             double l = v.lam[(int64_t)a * K + or_term_index(n1, n2, n3)];
-            gq += l * ((px[n1] * py[n2]) * pz[n3]);
-            if (n1) gr[0] += l * n1 * ((px[n1 - 1] * py[n2]) * pz[n3]);
-            if (n2) gr[1] += l * n2 * ((px[n1] * py[n2 - 1]) * pz[n3]);
-            if (n3) gr[2] += l * n3 * ((px[n1] * py[n2]) * pz[n3 - 1]);
+            gq += adj_term(&v, l * ((px[n1] * py[n2]) * pz[n3]));
+            if (n1) gr[0] += adj_term(&v, l * n1 * ((px[n1 - 1] * py[n2]) * pz[n3]));
+            if (n2) gr[1] += adj_term(&v, l * n2 * ((px[n1] * py[n2 - 1]) * pz[n3]));
+            if (n3) gr[2] += adj_term(&v, l * n3 * ((px[n1] * py[n2]) * pz[n3 - 1]));
           }
     }
     double h = 0.5 * s->P.lB;
     if (dEdq) dEdq[k] = h * (phi[k] + v.dq[k] + gq);
     if (dEdr)
-      for (int c = 0; c < 3; ++c) dEdr[3 * k + c] = h * (tgt[3 * k + c] + v.src[3 * k + c] + s->q[k] * gr[c]);
+      for (int c = 0; c < 3; ++c)
+        dEdr[3 * k + c] = h * (tgt[3 * k + c] + v.src[3 * k + c] + adj_term(&v, s->q[k]) * gr[c]);
   }
   free(v.lam);
   free(v.src);
@@ -1186,6 +1192,10 @@ int or_forces(or_sys* s, double* dEdr, double* dEdq) {
   free(tgt);
   return OR_OK;
 }
+
+int or_forces(or_sys* s, double* dEdr, double* dEdq) { return or_forces_impl(s, dEdr, dEdq, 0); }
+
+int or_forces_abs(or_sys* s, double* Ar, double* Aq) { return or_forces_impl(s, Ar, Aq, 1); }
 
 /* ------------------------------------------------------------------------- */
 /* Potential and its gradient at x (same traversal and exclusions as or_phi). */

@@ -147,6 +147,13 @@ int or_potentials(or_sys* s, double* v_tree, double* v_direct);
    fixed: dEdr (n x 3) = dE/dr_k, dEdq (n) = dE/dq_k for every charge (ions,
    fixed charges and images treated as independent).  Needs p <= OR_PMAX - 1. */
 int or_forces(or_sys* s, double* dEdr, double* dEdq);
+/* The same adjoint with every term replaced by its magnitude: per component,
+   l_B/2 times the sum of |term| over everything that enters dE/dr_k and
+   dE/dq_k (target side, direct source side, and the cluster adjoints built
+   from |q_i T_n| and pushed down with |monomial derivatives|).  It is the
+   conditioning of the forces: rounding errors in these terms are bounded by a
+   multiple of it. */
+int or_forces_abs(or_sys* s, double* Ar, double* Aq);
 
 /* Potential and its gradient at x from all charges except the listed ones. */
 int or_phi_grad(or_sys* s, const double x[3], int n_excl, const int64_t* excl, double* phi, double g[3]);

@@ -38,6 +38,7 @@ class Params(C.Structure):
         ("images", C.c_int32), ("image_R", C.c_double), ("image_alpha", C.c_double),
         ("precision", C.c_int32), ("warps", C.c_int32), ("layout", C.c_int32),
         ("node_factor", C.c_double), ("hard_core", C.c_double), ("fixed_depth", C.c_int32),
+        ("fixed_direct", C.c_int32), ("round_limit", C.c_int32),
     ]
 
 
@@ -106,6 +107,8 @@ def lib():
         L.bhmc_batch_replica.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]
         L.bhmc_batch_step_mc.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
                                          C.c_uint64, C.POINTER(McStats)]
+        L.bhmc_batch_step_mc_records.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
+                                                 C.c_uint64, C.POINTER(McStats), C.c_void_p]
         L.bhmc_batch_step_mc_spec.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_uint64),
                                               C.c_uint64, C.c_int32, C.POINTER(McStats)]
         _lib = L
@@ -158,6 +161,8 @@ def make_params(d: dict, precision=PREC_F32, warps=2, layout=LAYOUT_SOA, node_fa
     P.node_factor = d.get("node_factor", node_factor)
     P.hard_core = d.get("hard_core", 0.0) or 0.0
     P.fixed_depth = 1 if d.get("fixed_depth", False) else 0
+    P.fixed_direct = 1 if d.get("fixed_direct", False) else 0
+    P.round_limit = int(d.get("round_limit", 0))
     return P
 
 
@@ -400,6 +405,16 @@ def bhmc_batch_step_mc(h, n_rep, n_moves, step, seeds, move0=0):
     return [s.as_dict() for s in st]
 
 
+def bhmc_batch_step_mc_records(h, n_rep, n_moves, step, seeds, move0=0):
+    """(stats, records[n_rep, n_moves]) of one batched launch."""
+    sd = (C.c_uint64 * n_rep)(*[int(s) for s in seeds])
+    st = (McStats * n_rep)()
+    rec = np.zeros((n_rep, n_moves), dtype=RECORD_DTYPE)
+    _check(lib().bhmc_batch_step_mc_records(h, n_moves, step, sd, move0, st, C.c_void_p(rec.ctypes.data)),
+           "bhmc_batch_step_mc_records")
+    return [s.as_dict() for s in st], rec
+
+
 def bhmc_batch_step_mc_spec(h, n_rep, n_moves, step, seeds, move0=0, proposals=4):
     sd = (C.c_uint64 * n_rep)(*[int(s) for s in seeds])
     st = (McStats * n_rep)()
@@ -503,7 +518,9 @@ class Batch:
         c.h = bhmc_batch_replica(self.h, r)
         return c
 
-    def step_mc(self, n_moves, step, seeds, move0=0):
+    def step_mc(self, n_moves, step, seeds, move0=0, records=False):
+        if records:
+            return bhmc_batch_step_mc_records(self.h, self.n, n_moves, step, seeds, move0)
         return bhmc_batch_step_mc(self.h, self.n, n_moves, step, seeds, move0)
 
     def step_mc_spec(self, n_moves, step, seeds, move0=0, proposals=4):

@@ -118,6 +118,8 @@ static bhmc_status validate(const bhmc_params* P) {
     return BHMC_EINVAL;
   if (P->node_factor < 0.0) return BHMC_EINVAL;
   if (!(P->hard_core >= 0.0) || !std::isfinite(P->hard_core)) return BHMC_EINVAL;
+  if (P->fixed_direct != 0 && P->fixed_direct != 1) return BHMC_EINVAL;
+  if (P->round_limit < 0) return BHMC_EINVAL;
   return BHMC_OK;
 }
 
@@ -265,6 +267,10 @@ static void fill_view(SysDev& S, const bhmc_params* P, int64_t n_mob, int64_t n_
   S.n_mob = (int)n_mob;
   S.n_fix = (int)n_fix;
   S.n_tot = (int)(n_mob + n_fix + (P->images ? n_mob : 0));
+  S.fixed_direct = P->fixed_direct ? 1 : 0;
+  S.n_tree = S.n_tot - (S.fixed_direct ? (int)n_fix : 0);
+  S.move_rounds = P->round_limit > 0 ? P->round_limit : (1 << 22);
+  S.pass_pops = P->round_limit > 0 ? P->round_limit : (1 << 24);
   S.p = P->p;
   S.K = nterms(P->p);
   S.Kp = pad4(S.K);
@@ -396,7 +402,7 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
     cleanup();
     return rc;
   }
-  int n_list = (S.n_tot > S.Cs && S.Dmax > 0) ? 1 : 0;
+  int n_list = (S.n_tree > S.Cs && S.Dmax > 0) ? 1 : 0;
   int zero = 0;
   if (cudaMemcpyAsync(la, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cleanup();
@@ -427,7 +433,8 @@ static bhmc_status build_tree(bhmc_ctx* c, const double* q, const double* xyz, i
     std::swap(la, lb);
   }
   if (cudaMemcpyAsync(S.pool, &groups, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(S.order, perm, sizeof(int) * S.n_tot, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      (S.n_tree > 0 &&
+       cudaMemcpyAsync(S.order, perm, sizeof(int) * S.n_tree, cudaMemcpyDeviceToDevice, st) != cudaSuccess) ||
       build_leaves_moments(S, 8 * groups, perm, seg, dflags, level_begin.data(), (int)level_begin.size(), st) != cudaSuccess ||
       launch_hard_core_check(S, dflags, st) != cudaSuccess ||
       cudaMemcpyAsync(hflags, dflags, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -777,11 +784,13 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   bhmc_status rc = ctx_check(ctx);
   if (rc != BHMC_OK) return rc;
   const int warps = BHMC_ENERGY_WARPS;  // each warp evaluates 32 targets at a time
-  int grid = (ctx->S.n_tot + 32 * warps - 1) / (32 * warps);
-  grid = std::min(grid, 152 * 16);
+  int grid = (ctx->S.n_tree + 32 * warps - 1) / (32 * warps);
+  grid = std::max(1, std::min(grid, 152 * 16));
+  // one partial per warp, then q_f phi_f of the fixed charges held outside the tree
+  const int n_off = ctx->S.fixed_direct ? ctx->S.n_fix : 0;
   double* partial = nullptr;
   int* derr = nullptr;  // error flag, then three counters (8-byte aligned)
-  if (cudaMalloc(&partial, sizeof(double) * grid * warps) != cudaSuccess) return BHMC_ENOMEM;
+  if (cudaMalloc(&partial, sizeof(double) * ((size_t)grid * warps + n_off)) != cudaSuccess) return BHMC_ENOMEM;
   if (cudaMalloc(&derr, 32) != cudaSuccess) {
     cudaFree(partial);
     return BHMC_ENOMEM;
@@ -798,13 +807,18 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
       return BHMC_ENOMEM;
     }
   }
-  std::vector<double> h((size_t)grid * warps);
+  std::vector<double> h((size_t)grid * warps + n_off);
   int herr = 0;
   // the FP32 pass at p >= 6 evaluates from W32, refreshed here after moves
   const bool wform = ctx->S.prec == BHMC_PREC_F32 && ctx->S.p >= 6;
+  double* qphi = partial + (size_t)grid * warps;
   bool ok = (!wform || !ctx->w_stale || launch_wmirror(ctx->S, ctx->stream) == cudaSuccess) &&
             cudaMemsetAsync(derr, 0, 32, ctx->stream) == cudaSuccess &&
             dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
+            (n_off == 0 ||
+             (cudaMemsetAsync(qphi, 0, sizeof(double) * n_off, ctx->stream) == cudaSuccess &&
+              (!dphi || cudaMemsetAsync(dphi + ctx->S.n_mob, 0, sizeof(double) * n_off, ctx->stream) == cudaSuccess) &&
+              launch_fixed_targets(ctx->S, dphi, qphi, ctx->stream) == cudaSuccess)) &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                             ctx->stream) == cudaSuccess &&
             cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess;
@@ -871,12 +885,18 @@ bhmc_status bhmc_forces(bhmc_ctx* ctx, double* dEdr, double* dEdq, int32_t flags
   double* src = psi + n;
   double* odr = (flags & BHMC_DEVICE_PTRS) ? dEdr : src + 3 * n;
   double* odq = (flags & BHMC_DEVICE_PTRS) ? dEdq : odr + 3 * n;
-  const int grid = (int)std::min<size_t>((n + 127) / 128, 152 * 16);
+  const int grid = (int)std::max<size_t>(1, std::min<size_t>(((size_t)S.n_tree + 127) / 128, 152 * 16));
   cudaError_t e = cudaMemsetAsync(lam, 0, sizeof(double) * (nl + 4 * n), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess && S.fixed_direct && S.n_fix > 0) {
+    // the fixed charges outside the tree accumulate their target side
+    e = cudaMemsetAsync(phi + S.n_mob, 0, sizeof(double) * S.n_fix, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tg + 3 * (size_t)S.n_mob, 0, sizeof(double) * 3 * S.n_fix, ctx->stream);
+  }
   if (e == cudaSuccess) {
     e = by_p(ctx->P.p, [&](auto PC) { return launch_forces<PC.value>(S, grid, phi, tg, lam, psi, src, derr, ctx->stream); });
   }
+  if (e == cudaSuccess) e = launch_forces_fixed(S, phi, tg, psi, src, ctx->stream);
   if (e == cudaSuccess) e = launch_forces_push(S, phi, tg, lam, psi, src, odr, odq, ctx->stream);
   int herr = 0;
   if (e == cudaSuccess && !(flags & BHMC_DEVICE_PTRS)) {
@@ -1100,6 +1120,36 @@ static bhmc_status batch_prepare(bhmc_batch* B, uint64_t n_moves, double step, c
   B->h_args->step = step;
   B->h_args->seeds = B->d_seeds;
   B->h_args->order = B->d_order;
+  B->h_args->recs = nullptr;
+  return BHMC_OK;
+}
+
+// One replay of the batched graph; per-move records to `records` (host,
+// n_rep x n_moves) when it is non-null.
+static bhmc_status batch_run(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds, uint64_t move0,
+                             bhmc_mc_stats* stats, bhmc_move_record* records) {
+  bhmc_status rc0 = batch_prepare(B, n_moves, step, seeds, move0);
+  if (rc0 != BHMC_OK) return rc0;
+  const int n = (int)B->reps.size();
+  MoveRec* drec = nullptr;
+  const size_t nrec = (size_t)n * n_moves;
+  if (records && nrec) {
+    if (cudaMalloc(&drec, sizeof(MoveRec) * nrec) != cudaSuccess) return BHMC_ENOMEM;
+    B->h_args->recs = drec;
+  }
+  bhmc_status rc = BHMC_OK;
+  if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) rc = BHMC_ECUDA;
+  for (bhmc_ctx* c : B->reps) {
+    bhmc_status e = sync_err(c);
+    if (e != BHMC_OK && rc == BHMC_OK) rc = e;
+  }
+  if (rc == BHMC_OK && drec &&
+      cudaMemcpy(records, drec, sizeof(MoveRec) * nrec, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = BHMC_ECUDA;
+  B->h_args->recs = nullptr;
+  if (drec) cudaFree(drec);
+  if (rc != BHMC_OK) return rc;
+  if (stats) std::memcpy(stats, B->h_stats, sizeof(bhmc_mc_stats) * n);
   return BHMC_OK;
 }
 
@@ -1107,18 +1157,13 @@ extern "C" {
 
 bhmc_status bhmc_batch_step_mc(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
                                uint64_t move0, bhmc_mc_stats* stats) {
-  bhmc_status rc0 = batch_prepare(B, n_moves, step, seeds, move0);
-  if (rc0 != BHMC_OK) return rc0;
-  const int n = (int)B->reps.size();
-  CK(cudaGraphLaunch(B->graph, B->stream));
-  bhmc_status rc = BHMC_OK;
-  for (bhmc_ctx* c : B->reps) {
-    bhmc_status e = sync_err(c);
-    if (e != BHMC_OK && rc == BHMC_OK) rc = e;
-  }
-  if (rc != BHMC_OK) return rc;
-  if (stats) std::memcpy(stats, B->h_stats, sizeof(bhmc_mc_stats) * n);
-  return BHMC_OK;
+  return batch_run(B, n_moves, step, seeds, move0, stats, nullptr);
+}
+
+bhmc_status bhmc_batch_step_mc_records(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,
+                                       uint64_t move0, bhmc_mc_stats* stats, bhmc_move_record* records) {
+  if (!records) return BHMC_EINVAL;
+  return batch_run(B, n_moves, step, seeds, move0, stats, records);
 }
 
 bhmc_status bhmc_batch_step_mc_spec(bhmc_batch* B, uint64_t n_moves, double step, const uint64_t* seeds,

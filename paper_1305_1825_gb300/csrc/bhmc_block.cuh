@@ -159,7 +159,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
   };
   int rounds = 0;
   while (npop > 0) {
-    if (++rounds > (1 << 22)) {
+    if (++rounds > S.move_rounds) {
       err = BHMC_ETIMEOUT;
       break;
     }

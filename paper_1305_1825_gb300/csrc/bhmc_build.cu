@@ -1,5 +1,7 @@
 // bhmc_build.cu -- octree construction (Sec. 3.2), the stand-alone local
 // adjustment kernel behind bhmc_commit_move (Sec. 3.3), and direct sums.
+#include <algorithm>
+
 #include "bhmc_build.cuh"
 #include "bhmc_move.cuh"
 #include "bhmc_forces.cuh"
@@ -35,12 +37,19 @@ __global__ void k_init_charges(SysDev S, const double* q, const double* xyz, int
   }
 }
 
+// Keys of every charge; perm lists the charges of the tree (with fixed_direct
+// the fixed charges are left out and have no leaf).
 __global__ void k_keys(SysDev S, int* perm, int* flags) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.x * blockDim.x) {
     const unsigned long long k = point_key(S, S.px[j], S.py[j], S.pz[j]);
     if (k == 0ULL) atomicMax(&flags[0], 1);
     S.ckey[j] = k;
-    perm[j] = j;
+    if (off_tree(S, j)) {
+      S.leaf_of[j] = -1;
+      S.slot_of[j] = -1;
+    } else {
+      perm[S.fixed_direct && j >= S.n_mob ? j - S.n_fix : j] = j;
+    }
   }
 }
 
@@ -51,7 +60,7 @@ __global__ void k_init_root(SysDev S, int* seg) {
     const float c[3] = {(float)(S.root_lo[0] + 0.5 * S.root_side), (float)(S.root_lo[1] + 0.5 * S.root_side),
                         (float)(S.root_lo[2] + 0.5 * S.root_side)};
     S.nA[o] = o == 0 ? make_float4(c[0], c[1], c[2], h) : make_float4(0.f, 0.f, 0.f, 0.f);
-    S.nB[o] = make_int4(-1, o == 0 ? S.n_tot : 0, o == 0 ? 1 : 0, 0);
+    S.nB[o] = make_int4(-1, o == 0 ? S.n_tree : 0, o == 0 ? 1 : 0, 0);
     seg[o] = 0;
   }
   if (threadIdx.x == 0) {
@@ -457,6 +466,21 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
                                const double* psi, const double* src, double* dEdr, double* dEdq,
                                cudaStream_t st) {
   k_forces_push<<<grid_for(S.n_tot, 128), 128, 0, st>>>(S, phi, tgrad, lam, psi, src, dEdr, dEdq);
+  return cudaGetLastError();
+}
+
+// Fixed charges held outside the tree: blocks per fixed charge so that the
+// O(N) exact sums spread over the GPU.
+static inline dim3 fixed_grid(const SysDev& S) {
+  return dim3((unsigned)S.n_fix, (unsigned)std::max(1, std::min(64, (S.n_tot + 2047) / 2048)), 1);
+}
+cudaError_t launch_fixed_targets(const SysDev& S, double* phi, double* qphi, cudaStream_t st) {
+  if (S.fixed_direct && S.n_fix > 0) k_fixed_targets<<<fixed_grid(S), 256, 0, st>>>(S, phi, qphi);
+  return cudaGetLastError();
+}
+cudaError_t launch_forces_fixed(const SysDev& S, double* phi, double* tgrad, double* psi, double* src,
+                                cudaStream_t st) {
+  if (S.fixed_direct && S.n_fix > 0) k_forces_fixed<<<fixed_grid(S), 256, 0, st>>>(S, phi, tgrad, psi, src);
   return cudaGetLastError();
 }
 

@@ -24,5 +24,11 @@ cudaError_t launch_radial_counts(const SysDev& S, int nbins, double lo, double h
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st);
 cudaError_t launch_direct_energy(const SysDev& S, double* partial, int nblk, cudaStream_t st);
 cudaError_t launch_interleave(const SysDev& S, double* q, double* xyz, cudaStream_t st);
+// fixed charges held outside the tree (fixed_direct): exact potential at each
+// fixed charge (phi[f] may be null; phi and qphi accumulate, zeroed by the
+// caller; qphi[f] = q_f phi_f), and the exact pair terms of the adjoint pass
+cudaError_t launch_fixed_targets(const SysDev& S, double* phi, double* qphi, cudaStream_t st);
+cudaError_t launch_forces_fixed(const SysDev& S, double* phi, double* tgrad, double* psi, double* src,
+                                cudaStream_t st);
 
 }  // namespace bhmc

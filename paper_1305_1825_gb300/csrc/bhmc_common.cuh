@@ -33,6 +33,10 @@ __host__ __device__ constexpr int tidx(int n1, int n2, int n3) {
 // where x = x_hi + x_lo is the FP64 position split into two floats.
 struct SysDev {
   int n_mob, n_fix, n_tot;
+  int fixed_direct;         // 1: fixed charges outside the tree, exact terms everywhere
+  int n_tree;               // charges in the tree: n_tot, or n_tot - n_fix with fixed_direct
+  int move_rounds;          // iteration budgets: traversal rounds of a trial move,
+  int pass_pops;            // stack pops of one warp in the energy and force passes
   int p, K, Kp, N0, C, Dmax;
   int Cs;                   // split threshold: C, or 0 for the fixed-level tree
   int images, shell, prec, layout;
@@ -76,12 +80,15 @@ struct SysDev {
   int* err;
 };
 
+struct MoveRec;
+
 // Arguments of one batched launch (device memory).
 struct BatchArgs {
   unsigned long long n_moves, move0;
   double step;
   const unsigned long long* seeds;
   const int* order;  // replicas in the order blocks take them (largest first)
+  MoveRec* recs;     // null, or n_rep x n_moves per-move records (replica-major)
 };
 
 // --------------------------------------------------------------------------
@@ -201,6 +208,31 @@ __device__ __forceinline__ bool shell_ok(const SysDev& S, const double x[3]) {
 }
 
 __device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S.err, 0, code); }
+
+// Charge j is a fixed charge held outside the tree (fixed_direct).
+__host__ __device__ __forceinline__ bool off_tree(const SysDev& S, int j) {
+  return S.fixed_direct && j >= S.n_mob && j < S.n_mob + S.n_fix;
+}
+
+// Exact potential sum_f q_f / |r_f - x| at x of the fixed charges held outside
+// the tree, in FP64 with the operation order of the definition; g (may be
+// null) receives its gradient sum_f q_f (r_f - x) / |r_f - x|^3.
+__device__ __forceinline__ double fixed_phi(const SysDev& S, const double x[3], double* g) {
+  double phi = 0.0;
+  if (g) g[0] = g[1] = g[2] = 0.0;
+  for (int f = S.n_mob; f < S.n_mob + S.n_fix; ++f) {
+    const double e[3] = {__dsub_rn(S.px[f], x[0]), __dsub_rn(S.py[f], x[1]), __dsub_rn(S.pz[f], x[2])};
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+    const double r = __dsqrt_rn(r2);
+    const double qf = S.pq[f];
+    phi = __dadd_rn(phi, __ddiv_rn(qf, r));
+    if (g) {
+      const double r3 = __dmul_rn(r2, r);
+      for (int c = 0; c < 3; ++c) g[c] = __dadd_rn(g[c], __ddiv_rn(__dmul_rn(qf, e[c]), r3));
+    }
+  }
+  return phi;
+}
 
 // Binomial coefficient C(n, m), 0 <= m <= n <= 10.
 __device__ __forceinline__ int binom(int n, int m) {

@@ -22,6 +22,7 @@ struct MoveSetup {
   int outcome, flagged;
   int rej_dom, rej_shell, rej_img;
   double dE, alpha;
+  double fix;  // sum over the points of weight x exact potential of the off-tree fixed charges
 };
 
 struct MoveSh : MoveSetup {
@@ -43,6 +44,7 @@ struct MoveSh : MoveSetup {
   // index (~0: none)
   MoveSetup nxt;
   unsigned long long nxt_m;
+  int moved;  // ion moved by the last move (-1: none), which voids a setup of it
 };
 
 struct MoveStore {
@@ -267,6 +269,25 @@ static __device__ void setup_finish(const SysDev& S, MoveSetup& sh, int wb) {
     sh.outcome = sh.rej_dom ? BHMC_REJECT_DOMAIN
                             : sh.rej_shell ? BHMC_REJECT_OVERLAP : sh.rej_img ? BHMC_REJECT_DOMAIN : -1;
   }
+  // fixed charges held outside the tree: their exact terms at every point
+  // (FP64), one (point, fixed charge) pair per lane, summed over the warp
+  // (1/r from one FP64 rsqrt, within an ulp: far below the FP64 parity bar)
+  double fx = 0.0;
+  if (S.fixed_direct) {
+    const int s4 = lane & 3;
+    if (s4 < np) {
+      const double w = s4 == 0 ? -sh.q : (s4 == 1 ? sh.q : (s4 == 2 ? -sh.qa_img : (sh.rej_img ? 0.0 : sh.qb_img)));
+      const double* x = s4 == 0 ? sh.a : (s4 == 1 ? sh.b : (s4 == 2 ? sh.ai : sh.bi));
+      for (int f = S.n_mob + (lane >> 2); f < S.n_mob + S.n_fix; f += 8) {
+        const double e0 = __dsub_rn(S.px[f], x[0]), e1 = __dsub_rn(S.py[f], x[1]), e2 = __dsub_rn(S.pz[f], x[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+        fx = __dadd_rn(fx, __dmul_rn(__dmul_rn(w, S.pq[f]), rsqrt(r2)));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fx += __shfl_xor_sync(0xffffffffu, fx, o);
+  }
+  if (lane == 0) sh.fix = fx;
 }
 
 static __device__ void setup_move(const SysDev& S, MoveSetup& sh) {
@@ -287,7 +308,7 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
   block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr,
                                   sh.leafcnt, o);
   if (threadIdx.x == 0) {
-    double s = o.sum;
+    double s = o.sum + sh.fix;
     sh.cnt[0][0] = o.visited;
     sh.cnt[0][1] = o.accepted;
     sh.cnt[0][2] = o.pairs;
@@ -770,7 +791,9 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
   MoveSh& sh = st.sh;
   const int warp = threadIdx.x >> 5;
   ahead = ahead && blockDim.x == 256;
-  if (sh.nxt_m == m) {
+  // the look-ahead setup of move m is used unless move m - 1 moved its ion
+  // (both read after the barrier that ended move m - 1, so every thread agrees)
+  if (sh.nxt_m == m && sh.nxt.i != sh.moved) {
     constexpr int n = (int)(sizeof(MoveSetup) / sizeof(int));
     int* dst = reinterpret_cast<int*>(static_cast<MoveSetup*>(&sh));
     const int* src = reinterpret_cast<const int*>(&sh.nxt);
@@ -831,7 +854,9 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
     }
   }
   if (threadIdx.x == 0) {
-    if (sh.outcome == BHMC_ACCEPT && sh.nxt.i == sh.i) sh.nxt_m = ~0ULL;
+    // not a write of nxt_m here: thread 160 may still be finishing the
+    // look-ahead, and its nxt_m = m + 1 must not undo an invalidation
+    sh.moved = sh.outcome == BHMC_ACCEPT ? sh.i : -1;
     if (rec) {
       rec->i = sh.i;
       rec->r[0] = sh.b[0];
@@ -870,6 +895,17 @@ __device__ bool eval_grad(const SysDev& S, MoveStore& st, unsigned pmask) {
     for (int r = 0; r < 2; ++r) {
       sh.tphi[r] = o.phi[r];
       for (int c = 0; c < 3; ++c) sh.tgrad[r][c] = o.grad[r][c];
+    }
+    if (S.fixed_direct) {
+      // the off-tree fixed charges' exact potential and gradient at the point
+      // of each role (role 0: point 0 or 1, role 1: point 2 or 3)
+      for (int r = 0; r < 2; ++r) {
+        const int s = 2 * r + (((pmask >> (2 * r)) & 1u) ? 0 : 1);
+        if (!((pmask >> s) & 1u)) continue;
+        double g[3];
+        sh.tphi[r] += fixed_phi(S, sh.T.x[s], g);
+        for (int c = 0; c < 3; ++c) sh.tgrad[r][c] += g[c];
+      }
     }
     sh.cnt[0][4] = o.err;
     sh.hc_hit = o.overlap;
@@ -1097,8 +1133,9 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
         loc.flagged = 0;
     for (unsigned long long t = 0; t < args->n_moves; ++t) {
       if (*(volatile int*)S.err) break;
-      const int o = mc_move<P, Real, LAYOUT>(S, st, args->move0 + t, (unsigned)r, key, args->step,
-                                             nullptr, t + 1 < args->n_moves);
+      MoveRec* rec = args->recs ? args->recs + (size_t)r * args->n_moves + t : nullptr;
+      const int o = mc_move<P, Real, LAYOUT>(S, st, args->move0 + t, (unsigned)r, key, args->step, rec,
+                                             t + 1 < args->n_moves);
       if (o < 0) break;
       if (threadIdx.x == 0) tally(&loc, o, st.sh.flagged);
     }

@@ -2,6 +2,7 @@
 every failure is a status returned by the C-ABI)."""
 import numpy as np
 import pytest
+from tolerances import FLOOR32, REL
 
 from paper_1305_1825_gb300 import workloads as W
 
@@ -55,7 +56,7 @@ def test_root_leaf_and_theta_zero(bh, oracle_mod):
         b = wl["xyz"][i] + rng.uniform(-0.5, 0.5, 3)
         rc, dE, cnt = ctx.delta_energy(i, b)
         st, d = ref.delta_energy_direct(i, b)
-        assert cnt.accepted == 0 and abs(dE - d) <= 1e-5 * abs(d) + 5e-7 * ref.delta_energy(i, b).abs_sum
+        assert cnt.accepted == 0 and abs(dE - d) <= REL * abs(d) + FLOOR32 * ref.delta_energy(i, b).abs_sum
 
 
 def test_midplane_ties_tree(bh, oracle_mod):
@@ -173,3 +174,32 @@ def test_checkpoint_and_resume(bh):
     else:
         k = int(np.argmin(same))
         assert tail["flagged"][k] or r_res["flagged"][k]
+
+
+def test_bounded_loops_run_out_with_a_status(bh):
+    """A host-set budget of two traversal rounds makes the bounded device loops
+    run out on ordinary inputs: the trial-move evaluation and the energy pass
+    return BHMC_ETIMEOUT, a chain latches it (the next call returns
+    BHMC_ESTATE), and nothing faults or waits.  The same system with the
+    default budget evaluates normally."""
+    wl = W.colloid(n=2000, seed=5)
+    i, b = 3, wl["xyz"][3] + 0.1
+    ok = bh.Context(wl)
+    rc, dE, cnt = ok.delta_energy(i, b)
+    assert rc == 0 and cnt.visited > 2
+    ok.close()
+    wl["params"]["round_limit"] = 2
+    ctx = bh.Context(wl)
+    rc, dE, cnt = ctx.delta_energy(i, b)
+    assert rc == bh.ETIMEOUT
+    with pytest.raises(bh.BhmcError) as e:
+        ctx.energy()
+    assert e.value.status == bh.ETIMEOUT
+    with pytest.raises(bh.BhmcError) as e:
+        ctx.step_mc(50, 1.0, seed=3)
+    assert e.value.status == bh.ETIMEOUT
+    with pytest.raises(bh.BhmcError) as e:
+        ctx.energy()
+    assert e.value.status == bh.ESTATE
+    ctx.close()
+

@@ -15,7 +15,7 @@ from paper_1305_1825_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL, FLOOR32 = 1e-5, 5e-7
+from tolerances import FLOOR32, REL
 BENCH = dict(warps=8, layout=1)
 
 
@@ -83,18 +83,25 @@ def test_colloid_1e4_chain(bh, oracle_mod):
 
 @pytest.mark.parametrize("C", [8, 16])
 def test_batch_256_replicas_sampled(bh, oracle_mod, C):
+    """The benchmark's 256 replicas in the benchmark's launch configuration:
+    sampled replicas' per-move records (proposal, outcome, dE) against the
+    oracle chain move by move, up to the first flagged disagreement; positions
+    and trees at the end when no decision was flagged."""
     sizes = W.batch_sizes(256, seed=3)
     systems = W.batch(sizes=sizes, C=C)
     batch = bh.Batch(systems, **BENCH)
     seeds = [1000 + r for r in range(256)]
-    stats = batch.step_mc(150, 1.0, seeds)
+    stats, recs = batch.step_mc(150, 1.0, seeds, records=True)
     assert all(s["moves"] == 150 for s in stats)
     for r in (0, 77, int(np.argmax(sizes)), 255):
         ref = _oracle(oracle_mod, systems[r])
         orec = ref.mc_run(seeds[r], 150, replica=r)
+        upto = _compare_chain(recs[r], orec)
         flagged = int(orec["flagged"].sum())
+        assert upto == 150 or orec["flagged"][upto] or recs[r]["flagged"][upto]
         assert abs(stats[r]["accepted"] - int((orec["outcome"] == 0).sum())) <= flagged
         if flagged == 0:
+            assert upto == 150
             q, x = batch.replica(r).charges()
             assert np.array_equal(x, ref.charges()[1])
             assert batch.replica(r).export_tree() == ref.export_tree()
@@ -113,12 +120,17 @@ def test_large_colloid_1e6(bh, oracle_mod):
     assert np.array_equal(x, ref.charges()[1])
 
 
-def _check_potentials(ctx, ref, n, seed):
-    """Sampled per-charge treecode potentials phi_j (j excluded) against the oracle."""
+def _check_potentials(ctx, ref, n, seed, wl):
+    """Sampled per-charge treecode potentials phi_j (j excluded) against the
+    oracle; the macroion, held outside the tree, has the exact sum."""
     phi = ctx.potentials()
     q, x = ref.charges()
     rng = np.random.default_rng(seed)
-    for j in rng.choice(len(q), n, replace=False):
+    m = wl["n_mobile"]
+    for j in list(rng.choice(len(q), n, replace=False)) + [m]:
+        if wl["params"].get("fixed_direct") and m <= j < m + wl["n_fixed"]:
+            assert phi[j] == pytest.approx(ref.phi_direct(x[j], excl=[int(j)]), rel=1e-11)
+            continue
         e = ref.phi(x[j], excl=[int(j)])
         assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
     return phi, q
@@ -128,7 +140,7 @@ def test_colloid_1e4_potentials_and_energy(bh, oracle_mod):
     wl = W.colloid(n=10000, seed=2)
     ctx = bh.Context(wl, **BENCH)
     ref = _oracle(oracle_mod, wl)
-    phi, q = _check_potentials(ctx, ref, 200, seed=7)
+    phi, q = _check_potentials(ctx, ref, 200, seed=7, wl=wl)
     assert ctx.energy() == pytest.approx(0.5 * float(q @ phi), rel=1e-12)
 
 
@@ -137,4 +149,4 @@ def test_large_colloid_1e6_potentials(bh, oracle_mod):
     wl = W.large()
     ctx = bh.Context(wl, **BENCH)
     ref = _oracle(oracle_mod, wl)
-    _check_potentials(ctx, ref, 40, seed=8)
+    _check_potentials(ctx, ref, 40, seed=8, wl=wl)

@@ -4,11 +4,9 @@ Bars:
   * tree structure, leaf membership, interaction-list counters, proposals and
     accept/reject sequences: exact (decisions with |beta dE + ln alpha| < 1e-6
     are flagged and may differ);
-  * dE, FP32 traversal: |dE_gpu - dE_oracle| <= 1e-5 |dE_oracle| + 5e-7 * A, where
-    A = l_B sum over the interaction lists of |term|: each FP32 term (float-pair
-    difference, r^2, rsqrt, charge and weight products) carries a relative
-    error of at most about 8 * 2^-24 = 4.8e-7, so 5e-7 * A bounds the sum of
-    the per-term errors; the relative bar alone is unattainable when dE -> 0;
+  * dE, FP32 traversal: |dE_gpu - dE_oracle| <= 1e-5 |dE_oracle| + 1e-7 * A,
+    A = l_B sum over the interaction lists of |term| (derivation in
+    tests/tolerances.py);
   * dE, FP64 mode: |dE_gpu - dE_oracle| <= 1e-12 * A.
 """
 import numpy as np
@@ -18,7 +16,7 @@ from paper_1305_1825_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL, FLOOR32, FLOOR64 = 1e-5, 5e-7, 1e-12
+from tolerances import FLOOR32, FLOOR64, REL
 
 
 @pytest.fixture(scope="module")
@@ -36,6 +34,11 @@ def _oracle(oracle_mod, wl):
     return oracle_mod.System(wl["params"], wl["q"], wl["xyz"], wl["n_mobile"], wl["n_fixed"])
 
 
+def _off_tree(wl, j):
+    """Charge j is a fixed charge held outside the tree (exact interactions)."""
+    return bool(wl["params"].get("fixed_direct")) and wl["n_mobile"] <= j < wl["n_mobile"] + wl["n_fixed"]
+
+
 def _moves(wl, n, seed, scale=0.5):
     rng = np.random.default_rng(seed)
     for _ in range(n):
@@ -43,9 +46,9 @@ def _moves(wl, n, seed, scale=0.5):
         yield i, wl["xyz"][i] + rng.uniform(-scale, scale, 3)
 
 
-@pytest.mark.parametrize("kind", ["plain", "colloid"])
+@pytest.mark.parametrize("kind", ["plain", "colloid", "colloid-macroion-in-tree"])
 def test_build_matches_oracle(bh, oracle_mod, kind):
-    wl = W.plain(n=2000) if kind == "plain" else W.colloid(n=2000, seed=4)
+    wl = W.plain(n=2000) if kind == "plain" else W.colloid(n=2000, seed=4, fixed_direct=(kind == "colloid"))
     ctx = bh.Context(wl)
     ref = _oracle(oracle_mod, wl)
     tree, moms = ctx.export_tree(moments=True)
@@ -77,6 +80,28 @@ def test_delta_energy_matches_oracle(bh, oracle_mod, theta, p):
             assert abs(dE - e.dE) <= REL * abs(e.dE) + FLOOR32 * e.abs_sum, (dE, e.dE, e.abs_sum)
         assert n > 20
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("p", [2, 4])
+def test_delta_energy_macroion_in_tree(bh, oracle_mod, p, precision):
+    """The reading with the macroion as an ordinary tree charge (fixed_direct
+    off) stays available and matches the oracle under the same reading."""
+    wl = W.colloid(n=2000, seed=5, p=p, fixed_direct=False)
+    ref = _oracle(oracle_mod, wl)
+    ctx = bh.Context(wl, precision=precision, warps=4)
+    n = 0
+    for i, b in _moves(wl, 40, seed=90 + p):
+        rc, dE, cnt = ctx.delta_energy(i, b)
+        e = ref.delta_energy(i, b)
+        assert rc == e.status
+        if rc:
+            continue
+        n += 1
+        assert (cnt.visited, cnt.accepted, cnt.pairs) == (e.visited, e.accepted, e.pairs)
+        bar = FLOOR64 * e.abs_sum if precision else REL * abs(e.dE) + FLOOR32 * e.abs_sum
+        assert abs(dE - e.dE) <= bar, (dE, e.dE, e.abs_sum)
+    assert n > 20
 
 
 @pytest.mark.parametrize("p", [8, 10])
@@ -192,8 +217,9 @@ def test_mc_chain_plain_config(bh, oracle_mod, precision):
     assert st.energy == pytest.approx(orec["dE"][orec["outcome"] == 0].sum(), abs=1e-6 * orec["abs_sum"].max())
 
 
-def test_mc_chain_colloid(bh, oracle_mod):
-    wl = W.colloid(n=2000, seed=10)
+@pytest.mark.parametrize("fixed_direct", [True, False])
+def test_mc_chain_colloid(bh, oracle_mod, fixed_direct):
+    wl = W.colloid(n=2000, seed=10, fixed_direct=fixed_direct)
     ctx = bh.Context(wl, warps=4)
     ref = _oracle(oracle_mod, wl)
     st, rec = ctx.step_mc(600, 1.0, seed=2, records=True)
@@ -225,7 +251,7 @@ def test_batch_replicas_match_oracle_chains(bh, oracle_mod, warps):
 
 
 def test_full_energy(bh, oracle_mod):
-    for wl in (W.plain(n=1500), W.colloid(n=1200, seed=12)):
+    for wl in (W.plain(n=1500), W.colloid(n=1200, seed=12), W.colloid(n=1200, seed=12, fixed_direct=False)):
         ref = _oracle(oracle_mod, wl)
         for prec, tol in ((0, 2e-6), (1, 1e-12)):
             ctx = bh.Context(wl, precision=prec)
@@ -237,11 +263,12 @@ def test_full_energy(bh, oracle_mod):
             assert ctx.energy_direct() == pytest.approx(ref.energy_direct(), rel=1e-9)
 
 
+@pytest.mark.parametrize("fixed_direct", [True, False])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_energy_counters_match_oracle(bh, oracle_mod, precision):
+def test_energy_counters_match_oracle(bh, oracle_mod, precision, fixed_direct):
     """The full-energy pass's interaction lists, summed over all targets, equal
     the oracle's per-target traversals (target j excluded)."""
-    wl = W.colloid(n=600, seed=12)
+    wl = W.colloid(n=600, seed=12, fixed_direct=fixed_direct)
     ctx = bh.Context(wl, precision=precision, warps=2)
     ref = _oracle(oracle_mod, wl)
     E, cnt = ctx.energy_counters()
@@ -249,6 +276,8 @@ def test_energy_counters_match_oracle(bh, oracle_mod, precision):
     q, x = ref.charges()
     want = np.zeros(3, dtype=np.int64)
     for j in range(len(q)):
+        if _off_tree(wl, j):  # the macroion's potential is an exact sum, not a traversal
+            continue
         e = ref.phi(x[j], excl=[j])
         want += (e.visited, e.accepted, e.pairs)
     assert (cnt.visited, cnt.accepted, cnt.pairs) == tuple(int(v) for v in want)
@@ -283,7 +312,10 @@ def test_potentials_sampled(bh, oracle_mod, p):
     phi = ctx.potentials()
     q, x = ref.charges()
     rng = np.random.default_rng(p)
-    for j in rng.choice(len(q), 150, replace=False):
+    for j in list(rng.choice(len(q), 150, replace=False)) + [wl["n_mobile"]]:
+        if _off_tree(wl, j):  # the macroion: the exact sum over all other charges
+            assert phi[j] == pytest.approx(ref.phi_direct(x[j], excl=[int(j)]), rel=1e-12)
+            continue
         e = ref.phi(x[j], excl=[int(j)])
         assert abs(phi[j] - e.phi) <= REL * abs(e.phi) + FLOOR32 * e.abs_sum, (j, phi[j], e.phi)
 

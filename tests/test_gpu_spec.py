@@ -9,7 +9,7 @@ from paper_1305_1825_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-REL, FLOOR32 = 1e-5, 5e-7
+from tolerances import FLOOR32, REL
 
 
 @pytest.fixture(scope="module")
