@@ -49,15 +49,21 @@ struct bhmc_batch {
   BatchArgs* h_args = nullptr;
   unsigned long long* d_seeds = nullptr;
   int* d_order = nullptr;
-  int* d_next = nullptr;
+  int* d_sched = nullptr;  // replica claim flags, cursor, head, per-SM slots (BatchArgs)
+  int n_alone = -1;        // pairing of replicas per SM (BatchArgs::n_alone)
   bhmc_mc_stats* d_stats = nullptr;
   bhmc_mc_stats* h_stats = nullptr;
+  int* d_errs = nullptr;  // each replica's error word after a batched launch
+  int* h_errs = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int grid = 0;
   int warps = 1;
   int p = 4;
 };
+
+// Schedule words of a batched launch: claim flags, cursor, head, per-SM slots and heads.
+static size_t sched_bytes(int n_rep) { return sizeof(int) * ((size_t)n_rep + 2 + 2 * BHMC_SM_IDS); }
 
 #define CK(call)                              \
   do {                                        \
@@ -1015,10 +1021,12 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
       cudaMalloc(&B->d_args, sizeof(BatchArgs)) != cudaSuccess ||
       cudaMallocHost(&B->h_args, sizeof(BatchArgs)) != cudaSuccess ||
       cudaMalloc(&B->d_seeds, sizeof(unsigned long long) * n_rep) != cudaSuccess ||
-      cudaMalloc(&B->d_next, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&B->d_sched, sched_bytes(n_rep)) != cudaSuccess ||
       cudaMalloc(&B->d_order, sizeof(int) * n_rep) != cudaSuccess ||
       cudaMalloc(&B->d_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess ||
-      cudaMallocHost(&B->h_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess) {
+      cudaMallocHost(&B->h_stats, sizeof(bhmc_mc_stats) * n_rep) != cudaSuccess ||
+      cudaMalloc(&B->d_errs, sizeof(int) * n_rep) != cudaSuccess ||
+      cudaMallocHost(&B->h_errs, sizeof(int) * n_rep) != cudaSuccess) {
     bhmc_batch_destroy(B);
     return BHMC_ENOMEM;
   }
@@ -1042,7 +1050,15 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   B->grid = std::max(1, std::min(n_rep, std::max(1, occ) * std::max(1, sms)));
-  // Capture {args upload, work counter reset, persistent kernel, stats download}.
+  if (occ >= 2 && sms < n_rep && n_rep <= 2 * sms) {
+    // at most two replicas per SM: one block in each of the 2 x SMs slots; the
+    // 2 SMs - n largest replicas run alone, the others in large/small pairs
+    B->grid = 2 * sms;
+    B->n_alone = 2 * sms - n_rep;
+  }
+  // Capture {args upload, work counter and error words reset, persistent kernel,
+  // stats and error words download}: one replay reports every replica's error
+  // word without a copy per replica.
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1051,14 +1067,16 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
   }
   bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BatchArgs), cudaMemcpyHostToDevice, cs) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(B->d_next, 0, sizeof(int), cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(B->d_sched, 0, sched_bytes(n_rep), cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(B->d_errs, 0, sizeof(int) * n_rep, cs) == cudaSuccess;
   cudaError_t le = cudaSuccess;
   if (ok) {
-    le = by_p(B->p, [&](auto PC) { return launch_batch<PC.value>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_next, B->d_stats, cs); });
+    le = by_p(B->p, [&](auto PC) { return launch_batch<PC.value>(views[0], B->warps, B->d_views, n_rep, B->grid, B->d_args, B->d_stats, cs); });
   }
   ok = ok && le == cudaSuccess;
   ok = ok && cudaMemcpyAsync(B->h_stats, B->d_stats, sizeof(bhmc_mc_stats) * n_rep, cudaMemcpyDeviceToHost,
                              cs) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(B->h_errs, B->d_errs, sizeof(int) * n_rep, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
   const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
   ok = ok && ended && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
@@ -1080,10 +1098,12 @@ bhmc_status bhmc_batch_destroy(bhmc_batch* B) {
   cudaFree(B->d_args);
   cudaFreeHost(B->h_args);
   cudaFree(B->d_seeds);
-  cudaFree(B->d_next);
+  cudaFree(B->d_sched);
   cudaFree(B->d_order);
   cudaFree(B->d_stats);
   cudaFreeHost(B->h_stats);
+  cudaFree(B->d_errs);
+  cudaFreeHost(B->h_errs);
   delete B;
   return BHMC_OK;
 }
@@ -1121,6 +1141,13 @@ static bhmc_status batch_prepare(bhmc_batch* B, uint64_t n_moves, double step, c
   B->h_args->seeds = B->d_seeds;
   B->h_args->order = B->d_order;
   B->h_args->recs = nullptr;
+  B->h_args->errs = nullptr;
+  B->h_args->claimed = B->d_sched;
+  B->h_args->cursor = B->d_sched + n;
+  B->h_args->head = B->d_sched + n + 1;
+  B->h_args->sm_slot = B->d_sched + n + 2;
+  B->h_args->sm_head = B->d_sched + n + 2 + BHMC_SM_IDS;
+  B->h_args->n_alone = B->n_alone;
   return BHMC_OK;
 }
 
@@ -1137,11 +1164,21 @@ static bhmc_status batch_run(bhmc_batch* B, uint64_t n_moves, double step, const
     if (cudaMalloc(&drec, sizeof(MoveRec) * nrec) != cudaSuccess) return BHMC_ENOMEM;
     B->h_args->recs = drec;
   }
+  B->h_args->errs = B->d_errs;
   bhmc_status rc = BHMC_OK;
-  if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) rc = BHMC_ECUDA;
-  for (bhmc_ctx* c : B->reps) {
-    bhmc_status e = sync_err(c);
-    if (e != BHMC_OK && rc == BHMC_OK) rc = e;
+  if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess || cudaStreamSynchronize(B->stream) != cudaSuccess) {
+    for (bhmc_ctx* c : B->reps) c->sticky = BHMC_ECUDA;
+    rc = BHMC_ECUDA;
+  } else {
+    // every replica's error word came back with the replay; a device error
+    // latches in its context as the per-context calls do
+    for (int r = 0; r < n; ++r) {
+      const int e = B->h_errs[r];
+      if (e) {
+        B->reps[r]->sticky = e;
+        if (rc == BHMC_OK) rc = (bhmc_status)e;
+      }
+    }
   }
   if (rc == BHMC_OK && drec &&
       cudaMemcpy(records, drec, sizeof(MoveRec) * nrec, cudaMemcpyDeviceToHost) != cudaSuccess)

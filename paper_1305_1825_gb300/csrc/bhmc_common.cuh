@@ -89,7 +89,23 @@ struct BatchArgs {
   const unsigned long long* seeds;
   const int* order;  // replicas in the order blocks take them (largest first)
   MoveRec* recs;     // null, or n_rep x n_moves per-move records (replica-major)
+  int* errs;         // null, or n_rep: each replica's error word when its chain ends
+  // Which block runs which replica.  A block runs a replica's chain after
+  // setting its claim flag; blocks without one take entries of `order` from
+  // `cursor` (largest first) until every replica is claimed.  With n_alone >= 0
+  // (at most two replicas per SM) a block first prefers one replica: the first
+  // block on an SM the next entry of `order` (`head`), the second block the
+  // size-complement of its sibling's (entry n - 1 - (h - n_alone) for the
+  // sibling's entry h), or none when the sibling's is among the n_alone largest.
+  int* claimed;      // n_rep flags
+  int* cursor;
+  int* head;
+  int* sm_slot;      // blocks seen per SM id (BHMC_SM_IDS entries)
+  int* sm_head;      // entry + 1 taken by the first block of each SM id (0: not yet)
+  int n_alone;       // -1: no pairing
 };
+
+#define BHMC_SM_IDS 1024
 
 // --------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).

@@ -117,14 +117,13 @@ cudaError_t launch_spec_batch<BHMC_P>(const SysDev& S0, int warps, int proposals
 
 template <>
 cudaError_t launch_batch<BHMC_P>(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
-                                 const BatchArgs* args, int* next, bhmc_mc_stats* stats,
-                                 cudaStream_t st) {
+                                 const BatchArgs* args, bhmc_mc_stats* stats, cudaStream_t st) {
   if (S0.prec == BHMC_PREC_F64)
-    k_batch<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+    k_batch<BHMC_P, double, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, stats);
   else if (S0.layout == BHMC_LAYOUT_AOS)
-    k_batch<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+    k_batch<BHMC_P, float, BHMC_LAYOUT_AOS><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, stats);
   else
-    k_batch<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, next, stats);
+    k_batch<BHMC_P, float, BHMC_LAYOUT_SOA><<<grid, 32 * warps, 0, st>>>(views, n_rep, args, stats);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ cudaError_t launch_spec_batch(const SysDev& S0, int warps, int proposals, const 
                               const BatchArgs* args, bhmc_mc_stats* stats, cudaStream_t st);
 template <int P>
 cudaError_t launch_batch(const SysDev& S0, int warps, const SysDev* views, int n_rep, int grid,
-                         const BatchArgs* args, int* next, bhmc_mc_stats* stats, cudaStream_t st);
+                         const BatchArgs* args, bhmc_mc_stats* stats, cudaStream_t st);
 template <int P>
 int batch_occupancy(const SysDev& S0, int warps);
 template <int P>
@@ -59,7 +59,7 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
   template <> cudaError_t launch_spec_batch<P>(const SysDev&, int, int, const SysDev*, int,   \
                                               const BatchArgs*, bhmc_mc_stats*, cudaStream_t);  \
   template <> cudaError_t launch_batch<P>(const SysDev&, int, const SysDev*, int, int,       \
-                                              const BatchArgs*, int*, bhmc_mc_stats*,            \
+                                              const BatchArgs*, bhmc_mc_stats*,                  \
                                               cudaStream_t);                                     \
   template <> int batch_occupancy<P>(const SysDev&, int);                                    \
   template <> cudaError_t launch_energy<P>(const SysDev&, int, int, double*, double*, int*, unsigned long long*, \

@@ -1106,18 +1106,61 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step_mala(SysDev S, uns
 }
 
 
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// The replica this block prefers for its first chain (thread 0), n_rep for
+// none (see BatchArgs).  The second block on an SM waits for its sibling's
+// choice, which the sibling publishes right after taking it (both are
+// resident); the wait is bounded, and a block that gives up takes replicas
+// from the cursor like any other.
+__device__ __forceinline__ int batch_preferred(const BatchArgs* args, int n_rep) {
+  const unsigned id = sm_id();
+  if (id >= BHMC_SM_IDS) return n_rep;
+  const int slot = atomicAdd(&args->sm_slot[id], 1);
+  if (slot == 0) {
+    const int h = atomicAdd(args->head, 1);
+    atomicExch(&args->sm_head[id], h + 1);
+    return h < n_rep ? args->order[h] : n_rep;
+  }
+  if (slot != 1) return n_rep;
+  int v = 0;
+  for (int it = 0; it < (1 << 16); ++it) {
+    v = atomicAdd(&args->sm_head[id], 0);
+    if (v) break;
+    __nanosleep(256);
+  }
+  if (!v) return n_rep;
+  const int h = v - 1;
+  const int e = n_rep - 1 - (h - args->n_alone);
+  return (h >= args->n_alone && e >= 0 && e < n_rep) ? args->order[e] : n_rep;
+}
+
 template <int P, typename Real, int LAYOUT>
 __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* views, int n_rep, const BatchArgs* args,
-                                               int* next, bhmc_mc_stats* stats) {
+                                                                   bhmc_mc_stats* stats) {
   __shared__ MoveStore st;
   __shared__ int rep;
   __shared__ SysDev S;
   init_tables(st.sh, nterms(P));
+  bool first = true;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int q = atomicAdd(next, 1);
-      rep = q < n_rep ? args->order[q] : n_rep;
+      int r = n_rep;
+      if (first && args->n_alone >= 0) r = batch_preferred(args, n_rep);
+      if (r < n_rep && atomicExch(&args->claimed[r], 1) != 0) r = n_rep;
+      while (r >= n_rep) {  // the largest replica nobody has claimed yet
+        const int q = atomicAdd(args->cursor, 1);
+        if (q >= n_rep) break;
+        const int c = args->order[q];
+        if (atomicExch(&args->claimed[c], 1) == 0) r = c;
+      }
+      rep = r;
     }
+    first = false;
     __syncthreads();
     const int r = rep;
     if (r >= n_rep) break;
@@ -1142,6 +1185,7 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
     if (threadIdx.x == 0) {
       loc.energy = *S.energy;
       stats[r] = loc;
+      if (args->errs) args->errs[r] = *(volatile int*)S.err;
     }
     __syncthreads();
   }
