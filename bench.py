@@ -46,6 +46,8 @@ def parse(argv=None):
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per workload family instead of the headline line")
     ap.add_argument("--suite-large", action="store_true", help="include the 1e6-ion items in --suite")
+    ap.add_argument("--sections", default="plain,grid,edl,single,psweep,n0,fig6,naxis,mala,field,large",
+                    help="comma-separated --suite sections")
     return ap.parse_args(argv)
 
 
@@ -588,167 +590,261 @@ def _field_item(bh, name, wl, reps=3):
 
 
 def _eq4_1(bh, wl, warps):
-    """Eq. (4.1) relative error of the FP32 treecode against the exact sum (theta = 0,
-    FP64): V_i = q_i phi_i over every charge, over the mobile ions alone, and of the
-    FP64 treecode over every charge (the truncation error without FP32 rounding)."""
+    """Eq. (4.1), E = (sum_i |V_i - Vt_i|^2 / sum_i |V_i|^2)^(1/2) over the N
+    counterions i = 1..N (the mobile ions), V_i = l_B q_i phi_i with V exact
+    (theta = 0, FP64) and Vt the treecode under wl's reading of the macroion
+    (fixed_direct); also E of the FP64 traversal and E over every charge."""
     import numpy as np
     n, nt = wl["n_mobile"], wl["n_mobile"] + wl["n_fixed"]
+    q = np.asarray(wl["q"][:nt])
     ex = bh.Context(dict(wl, params=dict(wl["params"], theta=0.0)), precision=bh.PREC_F64, warps=8)
-    v = ex.potentials()[:nt] * np.asarray(wl["q"][:nt])
+    v = ex.potentials()[:nt] * q
     ex.close()
     tr = bh.Context(wl, warps=warps, layout=bh.LAYOUT_AOS)
-    vt = tr.potentials()[:nt] * np.asarray(wl["q"][:nt])
+    vt = tr.potentials()[:nt] * q
     tr.close()
     t64 = bh.Context(wl, precision=bh.PREC_F64, warps=8)
-    v64 = t64.potentials()[:nt] * np.asarray(wl["q"][:nt])
+    v64 = t64.potentials()[:nt] * q
     t64.close()
     rel = lambda a, b: float(np.sqrt(np.sum((a - b) ** 2) / np.sum(a ** 2)))
-    return rel(v, vt), rel(v[:n], vt[:n]), rel(v, v64)
+    return {"E_ions": rel(v[:n], vt[:n]), "E_ions_f64_traversal": rel(v[:n], v64[:n]),
+            "E_all_charges": rel(v, vt)}
+
+
+def _equilibrated(bh, wl, moves, warps):
+    """Positions of a configuration after `moves` trial moves of the workload's
+    own chain (one replica, persistent kernel): the paper measures Eq. (4.1) on
+    a snapshot of an equilibrated double layer."""
+    b = bh.Batch([wl], warps=warps, layout=bh.LAYOUT_AOS)
+    b.step_mc(moves, wl["step"], [wl["seed"]])
+    snap = b.replica(0).charges()[1][: wl["n_mobile"] + wl["n_fixed"]].copy()
+    b.close()
+    return snap
 
 
 def run_suite(args):
-    """One JSON line per workload family: the plain 2000-charge system, the 1e4
-    colloid over theta x p, adjoint forces and full energy at 1e5 (and 1e6), the
-    1e6-ion colloid, and Langevin moves.  Moves per second are CUDA-event times
-    on the library's stream; dE errors are measured on the GPU against its FP64
-    mode and the theta = 0 direct sum."""
+    """One JSON line per workload and setting, in sections (--sections):
+
+    plain   the 2000-charge system, one launch per move, FP32 and FP64
+    grid    the 1e4 colloid over theta x p, plain and 152 batched replicas
+    edl     the paper's hard-core double layer (Sec. 4) at N = 800 and 1e4 on
+            the adaptive and the fixed-level tree
+    single  one chain: one launch per move against a cluster of K CTAs
+    psweep  Eq. (4.1) over the counterions and moves/s against p = 0..10 at
+            theta 0.5 and 0.3 (Figs. 5 and 7), both readings of the macroion
+    n0      N_0(p) chosen by timing (Sec. 4)
+    fig6    RDF g(r) and ICDF Q(r) sampled inside the chains (Fig. 6):
+            treecode at p = 0, 1, 2, 4 against theta = 0 (direct)
+    naxis   Eq. (4.1) and moves/s against N = 100..1e4 (Figs. 5 and 7)
+    mala    Langevin moves
+    field   full energy and adjoint forces at 1e5 charges (1e6 with
+            --suite-large)
+    large   the 1e6-ion colloid (with --suite-large)
+
+    Moves per second are CUDA-event times on the library's stream; dE errors
+    are measured on the GPU against its FP64 mode and the theta = 0 sum."""
     import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
+    from paper_1305_1825_gb300 import autotune
     from paper_1305_1825_gb300 import bhmc as bh
     from paper_1305_1825_gb300 import workloads as W
     torch.cuda.set_device(0)
     lines = []
+    sections = set(args.sections.split(","))
+    AOS = bh.LAYOUT_AOS
 
     def emit(d):
         lines.append(d)
         print(json.dumps(d), flush=True)
 
-    # plain 2000-charge system: one launch per move, FP32 and FP64 traversal
-    wl = W.plain(n=2000)
-    emit({"suite": "plain-N2000", "theta": 0.5, "p": 4, "C": 8,
-          "gpu_plain_f32_moves_per_s": _plain_moves(bh, wl, 8, bh.LAYOUT_AOS, 1000),
-          "gpu_plain_f64_moves_per_s": _plain_moves(bh, wl, 8, bh.LAYOUT_AOS, 1000, precision=bh.PREC_F64),
-          "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 1, 200, 3.0),
-          "dE_error": _de_errors(bh, wl, 200, 11, 8, bh.LAYOUT_AOS)})
+    if "plain" in sections:
+        wl = W.plain(n=2000)
+        emit({"suite": "plain-N2000", "theta": 0.5, "p": 4, "C": 8,
+              "gpu_plain_f32_moves_per_s": _plain_moves(bh, wl, 8, AOS, 1000),
+              "gpu_plain_f64_moves_per_s": _plain_moves(bh, wl, 8, AOS, 1000, precision=bh.PREC_F64),
+              "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 1, 200, 3.0),
+              "dE_error": _de_errors(bh, wl, 200, 11, 8, AOS)})
 
-    # colloid, 1e4 ions: theta x p; batched = 152 replicas of the same size
-    for theta in (0.3, 0.5, 0.7):
-        for p in (2, 4, 6):
-            wl = W.colloid(n=10000, seed=2, theta=theta, p=p, C=args.C)
-            systems = [W.colloid(n=10000, seed=2000 + r, theta=theta, p=p, C=args.C) for r in range(152)]
-            rate_b, acc = _batched_moves(bh, systems, [2000 + r for r in range(152)], args.warps,
-                                         bh.LAYOUT_AOS, 400)
-            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400)
-            emit({"suite": "colloid-N1e4", "theta": theta, "p": p, "C": args.C,
-                  "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b,
-                  "batched_over_plain": rate_b / rate_p, "acceptance": acc,
-                  "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 2, 100, 2.0),
-                  "dE_error": _de_errors(bh, wl, 40, 100 + p, args.warps, bh.LAYOUT_AOS)})
-            del systems
+    if "grid" in sections:
+        for theta in (0.3, 0.5, 0.7):
+            for p in (2, 4, 6):
+                wl = W.colloid(n=10000, seed=2, theta=theta, p=p, C=args.C)
+                systems = [W.colloid(n=10000, seed=2000 + r, theta=theta, p=p, C=args.C) for r in range(152)]
+                rate_b, acc = _batched_moves(bh, systems, [2000 + r for r in range(152)], args.warps, AOS, 400)
+                rate_p = _plain_moves(bh, wl, args.warps, AOS, 400)
+                emit({"suite": "colloid-N1e4", "theta": theta, "p": p, "C": args.C,
+                      "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b,
+                      "batched_over_plain": rate_b / rate_p, "acceptance": acc,
+                      "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 2, 100, 2.0),
+                      "dE_error": _de_errors(bh, wl, 40, 100 + p, args.warps, AOS)})
+                del systems
 
-    # the paper's electric double layer with hard cores (Sec. 4, Eq. 2.1), on
-    # the adaptive tree and on the fixed-level tree of Sec. 3.2 (L_max = 6:
-    # leaves of side tau)
-    for n, reps in ((800, 152), (10000, 16)):
-        for Lmax in (0, 6):
-            wl = W.edl_hard(n=n, seed=8, Lmax=Lmax)
-            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 400 if n > 1000 else 1000)
-            systems = [W.edl_hard(n=n, seed=8000 + r, Lmax=Lmax) for r in range(reps)]
-            rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps,
-                                         bh.LAYOUT_AOS, 1000 if n <= 1000 else 400)
-            spec = {}
-            if reps * 8 <= 152:  # few replicas: a cluster of K CTAs per replica
-                for k in (4, 8):
-                    spec["gpu_batched_%d_replicas_clusters_of_%d_moves_per_s" % (reps, k)] = _spec_batched_moves(
-                        bh, systems, [8000 + r for r in range(reps)], args.warps, bh.LAYOUT_AOS, 4000, k)
-            del systems
-            emit({"suite": "edl-hard-N%d" % n, "tree": "fixed L_max=%d" % Lmax if Lmax else "adaptive C=8", **spec,
-                  "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
-                  "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
-                  "acceptance": acc,
-                  "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
+    if "edl" in sections:
+        # the paper's double layer with hard cores (Sec. 4, Eq. 2.1), on the
+        # adaptive tree and on the fixed-level tree of Sec. 3.2 (L_max = 6:
+        # leaves of side tau)
+        for n, reps in ((800, 152), (10000, 16)):
+            for Lmax in (0, 6):
+                wl = W.edl_hard(n=n, seed=8, Lmax=Lmax)
+                rate_p = _plain_moves(bh, wl, args.warps, AOS, 400 if n > 1000 else 1000)
+                systems = [W.edl_hard(n=n, seed=8000 + r, Lmax=Lmax) for r in range(reps)]
+                rate_b, acc = _batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps, AOS,
+                                             1000 if n <= 1000 else 400)
+                spec = {}
+                if reps * 8 <= 152:  # few replicas: a cluster of K CTAs per replica
+                    for k in (4, 8):
+                        spec["gpu_batched_%d_replicas_clusters_of_%d_moves_per_s" % (reps, k)] = \
+                            _spec_batched_moves(bh, systems, [8000 + r for r in range(reps)], args.warps, AOS, 4000, k)
+                del systems
+                emit({"suite": "edl-hard-N%d" % n, "tree": "fixed L_max=%d" % Lmax if Lmax else "adaptive C=8",
+                      **spec, "theta": 0.5, "p": 2, "C": 8, "tau": 4.0, "lB": 7.14,
+                      "gpu_plain_moves_per_s": rate_p, "gpu_batched_%d_replicas_moves_per_s" % reps: rate_b,
+                      "acceptance": acc,
+                      "oracle_moves_per_s": None if args.no_cpu_baseline else _oracle_moves(wl, 8, 200, 2.0)})
 
-    # one chain (the paper's setting): one launch per trial move against one
-    # persistent launch of a cluster of K CTAs that evaluates K trials at once
-    for wl in (W.edl_hard(n=800, seed=8), W.edl_hard(n=10000, seed=8), W.colloid(n=10000, seed=2, C=args.C)):
-        line = {"suite": "single-chain-" + wl["name"], "theta": wl["params"]["theta"], "p": wl["params"]["p"],
-                "gpu_plain_moves_per_s": _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 1000)}
-        for k in (1, 2, 4, 8):
-            rate, acc = _spec_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 20000, k)
-            line["gpu_cluster_%d_proposals_moves_per_s" % k] = rate
-            line["acceptance"] = acc
-        emit(line)
+    if "single" in sections:
+        # one chain (the paper's setting): one launch per trial move against one
+        # persistent launch of a cluster of K CTAs that evaluates K trials at once
+        for wl in (W.edl_hard(n=800, seed=8), W.edl_hard(n=10000, seed=8), W.colloid(n=10000, seed=2, C=args.C)):
+            line = {"suite": "single-chain-" + wl["name"], "theta": wl["params"]["theta"], "p": wl["params"]["p"],
+                    "gpu_plain_moves_per_s": _plain_moves(bh, wl, args.warps, AOS, 1000)}
+            for k in (1, 2, 4, 8):
+                rate, acc = _spec_moves(bh, wl, args.warps, AOS, 20000, k)
+                line["gpu_cluster_%d_proposals_moves_per_s" % k] = rate
+                line["acceptance"] = acc
+            emit(line)
 
-    # error and speed against the multipole order (the paper's Figs. 5 and 7):
-    # Eq. (4.1) E = sqrt(sum_i |V_i - Vt_i|^2 / sum_i |V_i|^2) over the ions,
-    # V_i = q_i phi_i over every charge (ions and the macroion; the ions alone
-    # reported beside it), V exact (theta = 0, FP64), Vt the FP32 treecode,
-    # on the double layer;
-    # the moves/s lines start from the workload's own configuration
-    # on a snapshot of an equilibrated chain (as the paper's), not the start
-    base = W.edl_hard(n=800, seed=8)
-    eqb = bh.Batch([base], warps=args.warps, layout=bh.LAYOUT_AOS)
-    eqb.step_mc(200000, base["step"], [8])
-    snap = eqb.replica(0).charges()[1][: base["n_mobile"] + base["n_fixed"]].copy()
-    eqb.close()
-    for theta in (0.5, 0.3):
-        for pp in range(0, 11):
-            wl = W.edl_hard(n=800, seed=8, theta=theta, p=pp)
-            wl["xyz"] = snap
-            E, E_ions, E64 = _eq4_1(bh, wl, args.warps)
-            rate_p = _plain_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 1000)
-            systems = [W.edl_hard(n=800, seed=8000 + r, theta=theta, p=pp) for r in range(152)]
-            rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps,
-                                       bh.LAYOUT_AOS, 1000)
-            del systems
-            emit({"suite": "p-sweep-edl-N800", "theta": theta, "p": pp, "E_eq4_1": E,
-                  "E_eq4_1_ions_only": E_ions, "E_eq4_1_f64_traversal": E64, "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b})
-    # the minimum expansion number N0 (Sec. 3.2): small clusters summed directly
-    for pp in (2, 4):
-        for n0 in (0, 4, 8, 16):
+    snap = None
+    if sections & {"psweep", "n0"}:
+        # a snapshot of an equilibrated chain of the N = 800 double layer
+        snap = _equilibrated(bh, W.edl_hard(n=800, seed=8), 200000, args.warps)
+
+    if "psweep" in sections:
+        # error and speed against the multipole order (Figs. 5 and 7): E of
+        # Eq. (4.1) over the 800 counterions with the macroion's interactions
+        # exact (the reading adopted) and with the macroion as a tree charge,
+        # and moves/s of the workload's own chains (plain and 152 replicas)
+        for theta in (0.5, 0.3):
+            for pp in range(0, 11):
+                wl = W.edl_hard(n=800, seed=8, theta=theta, p=pp)
+                wl["xyz"] = snap
+                e = _eq4_1(bh, wl, args.warps)
+                e_tree = _eq4_1(bh, W.edl_hard(n=800, seed=8, theta=theta, p=pp, fixed_direct=False) | {"xyz": snap},
+                                args.warps)
+                rate_p = _plain_moves(bh, wl, args.warps, AOS, 1000)
+                systems = [W.edl_hard(n=800, seed=8000 + r, theta=theta, p=pp) for r in range(152)]
+                rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps, AOS, 1000)
+                del systems
+                emit({"suite": "p-sweep-edl-N800", "theta": theta, "p": pp,
+                      "E_eq4_1_counterions": e["E_ions"], "E_eq4_1_counterions_f64_traversal": e["E_ions_f64_traversal"],
+                      "E_eq4_1_all_charges": e["E_all_charges"],
+                      "E_eq4_1_counterions_macroion_in_tree": e_tree["E_ions"],
+                      "E_eq4_1_all_charges_macroion_in_tree": e_tree["E_all_charges"],
+                      "gpu_plain_moves_per_s": rate_p, "gpu_batched_152_replicas_moves_per_s": rate_b})
+
+    if "n0" in sections:
+        # N_0(p) by timing (Sec. 4: N_0 chosen from measured times for each p)
+        systems = [W.edl_hard(n=800, seed=8000 + r) for r in range(152)]
+        seeds = [8000 + r for r in range(152)]
+        res = autotune.tune_n0(systems, seeds, warps=args.warps, layout=AOS, moves=1000)
+        del systems
+        for pp, d in sorted(res.items()):
             wl = W.edl_hard(n=800, seed=8, theta=0.5, p=pp)
             wl["xyz"] = snap
-            wl["params"]["N0"] = n0
-            E, E_ions, _ = _eq4_1(bh, wl, args.warps)
-            systems = []
-            for r in range(152):
-                w2 = W.edl_hard(n=800, seed=8000 + r, theta=0.5, p=pp)
-                w2["params"]["N0"] = n0
-                systems.append(w2)
-            rate_b, _ = _batched_moves(bh, systems, [8000 + r for r in range(152)], args.warps,
-                                       bh.LAYOUT_AOS, 1000)
+            wl["params"]["N0"] = d["chosen"]
+            e = _eq4_1(bh, wl, args.warps)
+            emit({"suite": "N0-by-timing-edl-N800", "theta": 0.5, "p": pp, "N0_chosen": d["chosen"],
+                  "gpu_batched_152_replicas_moves_per_s": {str(k): v for k, v in d["rates"].items()},
+                  "E_eq4_1_counterions_at_chosen_N0": e["E_ions"]})
+
+    if "fig6" in sections:
+        # Fig. 6: g(r) and Q(r) of the N = 800 double layer averaged over the
+        # chains (sampled inside the persistent kernel every 100 moves after a
+        # burn-in), the treecode at theta = 0.5 and p = 0, 1, 2, 4 against
+        # theta = 0 (every interaction direct)
+        nb, lo, hi, reps = 46, 32.0, 78.0, 152
+        qm = -1600.0
+
+        def profiles(theta, pp, burn=20000, moves=100000):
+            systems = [W.edl_hard(n=800, seed=8000 + r, theta=theta, p=pp) for r in range(reps)]
+            seeds = [8000 + r for r in range(reps)]
+            b = bh.Batch(systems, warps=args.warps, layout=AOS)
+            b.step_mc(burn, 2.0, seeds)
+            b.set_radial_sampling(nb, lo, hi, 100)
+            t0 = time.perf_counter()
+            b.step_mc(moves, 2.0, seeds, move0=burn)
+            dt = time.perf_counter() - t0
+            c, q, ns = b.radial_samples()
+            b.close()
+            halves = []
+            for part in (slice(0, reps // 2), slice(reps // 2, reps)):
+                halves.append(bh.radial_profiles(c[part].sum(0), q[part].sum(0), lo, hi, int(ns[part].sum()), q_fixed=qm))
+            full = bh.radial_profiles(c.sum(0), q.sum(0), lo, hi, int(ns.sum()), q_fixed=qm)
+            return full, halves, reps * moves / dt
+
+        (ref, ref_h, rate0) = profiles(0.0, 0)
+        noise_g = float(np.abs(ref_h[0][1] - ref_h[1][1]).max())
+        noise_Q = float(np.abs(ref_h[0][3] - ref_h[1][3]).max())
+        for pp in (0, 1, 2, 4):
+            full, _, rate = profiles(0.5, pp)
+            emit({"suite": "fig6-rdf-icdf-edl-N800", "theta": 0.5, "p": pp, "bins": nb, "r_range": [lo, hi],
+                  "samples_per_replica": 1000, "replicas": reps,
+                  "max_abs_dg_vs_direct": float(np.abs(full[1] - ref[1]).max()),
+                  "max_abs_dQ_vs_direct": float(np.abs(full[3] - ref[3]).max()),
+                  "direct_half_vs_half_max_abs_dg": noise_g, "direct_half_vs_half_max_abs_dQ": noise_Q,
+                  "g_first_bins": [float(v) for v in full[1][:6]], "g_direct_first_bins": [float(v) for v in ref[1][:6]],
+                  "Q_at_a_plus_4": float(full[3][3]), "Q_direct_at_a_plus_4": float(ref[3][3]),
+                  "moves_per_s_with_sampling": rate, "moves_per_s_direct_with_sampling": rate0})
+
+    if "naxis" in sections:
+        # Eq. (4.1) over the counterions and moves/s against N (Figs. 5 and 7)
+        for n in (100, 300, 1000, 3000, 10000):
+            base = W.edl_hard(n=n, seed=8)
+            sn = _equilibrated(bh, base, 100000, args.warps)
+            line = {"suite": "N-axis-edl", "N": n, "p": 2}
+            for theta in (0.5, 0.3):
+                wl = W.edl_hard(n=n, seed=8, theta=theta, p=2)
+                wl["xyz"] = sn
+                line["E_eq4_1_counterions_theta%.1f" % theta] = _eq4_1(bh, wl, args.warps)["E_ions"]
+            reps = 152 if n <= 3000 else 16
+            systems = [W.edl_hard(n=n, seed=8000 + r) for r in range(reps)]
+            line["gpu_batched_%d_replicas_moves_per_s" % reps], line["acceptance"] = _batched_moves(
+                bh, systems, [8000 + r for r in range(reps)], args.warps, AOS, 1000 if n <= 3000 else 400)
             del systems
-            emit({"suite": "N0-sweep-edl-N800", "theta": 0.5, "p": pp, "N0": n0,
-                  "E_eq4_1": E, "E_eq4_1_ions_only": E_ions,
-                  "gpu_batched_152_replicas_moves_per_s": rate_b})
+            line["gpu_plain_moves_per_s"] = _plain_moves(bh, base, args.warps, AOS, 400)
+            if not args.no_cpu_baseline:
+                line["oracle_moves_per_s"] = _oracle_moves(base, 8, 100, 1.0)
+            emit(line)
 
-    # Langevin moves on the 1e4 colloid (step 0.05)
-    wl = W.colloid(n=10000, seed=2)
-    ctx = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
-    ctx.step_mala(20, 0.05, seed=3)
-    ms, (st, _) = _ev_time(lambda: ctx.step_mala(400, 0.05, seed=3, move0=20))
-    emit({"suite": "mala-colloid-N1e4", "tau": 0.05, "gpu_moves_per_s": 400 / (ms / 1e3),
-          "acceptance": st.accepted / max(st.moves, 1)})
-    ctx.close()
+    if "mala" in sections:
+        wl = W.colloid(n=10000, seed=2)
+        ctx = bh.Context(wl, warps=args.warps, layout=AOS)
+        ctx.step_mala(20, 0.05, seed=3)
+        ms, (st, _) = _ev_time(lambda: ctx.step_mala(400, 0.05, seed=3, move0=20))
+        emit({"suite": "mala-colloid-N1e4", "tau": 0.05, "gpu_moves_per_s": 400 / (ms / 1e3),
+              "acceptance": st.accepted / max(st.moves, 1)})
+        ctx.close()
 
-    # adjoint forces and full energy
-    emit(_field_item(bh, "field-uniform-N1e5", W.uniform(n=100000)))
-    emit(_field_item(bh, "field-colloid-scaled-N1e5", W.colloid_scaled(n=100000)))
-    if args.suite_large:
+    if "field" in sections:
+        emit(_field_item(bh, "field-uniform-N1e5", W.uniform(n=100000)))
+        emit(_field_item(bh, "field-colloid-scaled-N1e5", W.colloid_scaled(n=100000)))
+        if args.suite_large:
+            emit(_field_item(bh, "field-large-N1e6", W.large(), reps=2))
+
+    if "large" in sections and args.suite_large:
         wl = W.large()
-        emit(_field_item(bh, "field-large-N1e6", wl, reps=2))
-        ctx = bh.Context(wl, warps=args.warps, layout=bh.LAYOUT_AOS)
+        ctx = bh.Context(wl, warps=args.warps, layout=AOS)
         ctx.step_mc(20, 1.0, seed=9)
         ms, st = _ev_time(lambda: ctx.step_mc(500, 1.0, seed=9, move0=20))
         ctx.close()
-        b = bh.Batch([wl], warps=args.warps, layout=bh.LAYOUT_AOS)
+        b = bh.Batch([wl], warps=args.warps, layout=AOS)
         b.step_mc(100, 1.0, [9])
         ms_b, _ = _ev_time(lambda: b.step_mc(4000, 1.0, [9], move0=100))
         b.close()
-        rate4, acc4 = _spec_moves(bh, wl, args.warps, bh.LAYOUT_AOS, 4000, 4)
-        emit({"suite": "large-N1e6", "theta": 0.5, "p": 6, "C": 8, "charges": 2000001,
+        rate4, acc4 = _spec_moves(bh, wl, args.warps, AOS, 4000, 4)
+        emit({"suite": "large-N1e6", "theta": 0.5, "p": 6, "C": 8, "charges_in_tree": 2000000,
               "gpu_plain_moves_per_s": 500 / (ms / 1e3),
               "gpu_persistent_1_replica_moves_per_s": 4000 / (ms_b / 1e3),
               "gpu_cluster_4_proposals_moves_per_s": rate4, "acceptance": acc4})

@@ -211,6 +211,34 @@ bhmc_status bhmc_step_mala(bhmc_ctx* ctx, uint64_t n_moves, double tau, uint64_t
 bhmc_status bhmc_radial_counts(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
                                double* charge);
 
+/* Radial sampling inside the chains (Sec. 4, Fig. 6: the RDF and ICDF are
+   averages over the configurations of the Markov chain).  With nbins > 0 the
+   context keeps a running histogram of its mobile ions (bins as in
+   bhmc_radial_counts, built from the current configuration by this call and
+   updated by every committed move on the device), and every chain call
+   (bhmc_step_mc, bhmc_step_mc_spec, bhmc_step_mala) adds it to device
+   accumulators after each move m with (m + 1) % every == 0 (m the absolute
+   move index, so the samples do not depend on how the chain is split into
+   calls).  The accumulators start at zero here; nbins = 0 switches sampling
+   off.  EINVAL for nbins outside [0, 2^20], every < 0, r_hi <= r_lo, or a
+   replica of a batch (use bhmc_batch_set_radial_sampling). */
+bhmc_status bhmc_set_radial_sampling(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t every);
+/* The accumulated samples: counts[nbins] and charge[nbins] (host; the sums of
+   the running histogram over the samples) and the number of samples.
+   BHMC_ESTATE if sampling is off. */
+bhmc_status bhmc_get_radial_samples(bhmc_ctx* ctx, int64_t* counts, double* charge, int64_t* n_samples);
+/* RDF and ICDF of Sec. 4 from accumulated counts (host arithmetic only, no
+   device call): <N_k> = counts[k] / n_samples, V_k = (4/3) pi (r_{k+1}^3 -
+   r_k^3) with r_k = r_lo + k (r_hi - r_lo) / nbins;
+   g[k] = (<N_k>/V_k) / sum_j (<N_j>/V_j) (the bins normalised to sum one);
+   Q[k] = q_fixed + sum_{j <= k} charge[j] / n_samples, the charge inside the
+   outer edge r_out[k] of bin k (Q(a) = Q_M and Q(R_cell) = 0 for the
+   neutral cell of Sec. 4); r_mid[k] is the bin centre.  All arrays have nbins
+   entries.  EINVAL for nbins < 1, r_hi <= r_lo or n_samples < 1. */
+bhmc_status bhmc_radial_profiles(int32_t nbins, double r_lo, double r_hi, const int64_t* counts,
+                                 const double* charge, int64_t n_samples, double q_fixed, double* r_mid, double* g,
+                                 double* r_out, double* Q);
+
 /* Running energy (sum of accepted dE since creation, or rebased by set). */
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E);
 bhmc_status bhmc_set_energy(bhmc_ctx* ctx, double E);
@@ -275,6 +303,13 @@ bhmc_status bhmc_batch_create(int32_t n_rep, const bhmc_params* params, const in
 bhmc_status bhmc_batch_destroy(bhmc_batch* batch);
 /* Borrowed context of replica r (valid until the batch is destroyed; do not destroy it). */
 bhmc_status bhmc_batch_replica(bhmc_batch* batch, int32_t r, bhmc_ctx** ctx);
+/* bhmc_set_radial_sampling for every replica of the batch (the batched chain
+   calls then sample as the single-context calls do). */
+bhmc_status bhmc_batch_set_radial_sampling(bhmc_batch* batch, int32_t nbins, double r_lo, double r_hi,
+                                           int64_t every);
+/* Per replica: counts[r * nbins + k], charge[r * nbins + k], n_samples[r]. */
+bhmc_status bhmc_batch_get_radial_samples(bhmc_batch* batch, int64_t* counts, double* charge,
+                                          int64_t* n_samples);
 /* bhmc_radial_counts summed over every replica of the batch. */
 bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
                                      double* charge);

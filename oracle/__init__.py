@@ -113,6 +113,9 @@ def lib():
         L.or_potentials.argtypes = [C.c_void_p, _dp, _dp]
         L.or_forces.argtypes = [C.c_void_p, _dp, _dp]
         L.or_forces_abs.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_radial_counts.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, _i64p, _dp]
+        L.or_radial_profiles.argtypes = [C.c_int, C.c_double, C.c_double, _i64p, _dp, C.c_int64, C.c_double,
+                                         _dp, _dp, _dp, _dp]
         L.or_ion_energy_grad.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, _dp]
         L.or_phi_grad.argtypes = [C.c_void_p, _dp, C.c_int, _i64p, _dp, _dp]
         L.or_mala_run.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64,
@@ -315,6 +318,16 @@ class System:
             raise ValueError("or_forces_abs failed with status %d" % rc)
         return g, dq
 
+    def radial_counts(self, nbins, r_lo, r_hi, counts=None, charge=None):
+        """Add the mobile ions' radial bins (Sec. 4) to counts / charge (new arrays if None)."""
+        counts = np.zeros(nbins, dtype=np.int64) if counts is None else counts
+        charge = np.zeros(nbins) if charge is None else charge
+        rc = lib().or_radial_counts(self._h, nbins, r_lo, r_hi, counts.ctypes.data_as(_i64p),
+                                    charge.ctypes.data_as(_dp))
+        if rc:
+            raise ValueError("or_radial_counts failed with status %d" % rc)
+        return counts, charge
+
     def export_tree(self):
         """{(depth, key): (is_leaf, count, members-tuple or None)}"""
         cap = 8 * self.n_charges + 64
@@ -349,3 +362,17 @@ class System:
     def point_key(self, x) -> int:
         x, xp = _d(x)
         return int(lib().or_point_key(self._h, xp))
+
+
+def radial_profiles(counts, charge, r_lo, r_hi, n_samples, q_fixed=0.0):
+    """(bin centres, g, outer edges, Q) of Sec. 4 from accumulated counts (or_radial_profiles)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    charge = np.ascontiguousarray(charge, dtype=np.float64)
+    n = len(counts)
+    out = [np.zeros(n) for _ in range(4)]
+    rc = lib().or_radial_profiles(n, r_lo, r_hi, counts.ctypes.data_as(_i64p), charge.ctypes.data_as(_dp),
+                                  int(n_samples), q_fixed, *[o.ctypes.data_as(_dp) for o in out])
+    if rc:
+        raise ValueError("or_radial_profiles failed with status %d" % rc)
+    return tuple(out)
+

@@ -1402,3 +1402,40 @@ int or_ion_energy_grad(or_sys* s, int64_t i, const double x[3], double* U, doubl
   if (i < 0 || i >= s->n_mob) return OR_EINVAL;
   return or_ion_energy(s, i, x, U, gU);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Radial distribution and integrated charge of Sec. 4 (Fig. 6). */
+int or_radial_counts(const or_sys* s, int nbins, double r_lo, double r_hi, int64_t* counts, double* charge) {
+  if (nbins < 1 || !(r_hi > r_lo)) return OR_EINVAL;
+  double w = (r_hi - r_lo) / (double)nbins;
+  for (int64_t i = 0; i < s->n_mob; ++i) {
+    double x = s->x[3 * i], y = s->x[3 * i + 1], z = s->x[3 * i + 2];
+    double r = sqrt((x * x + y * y) + z * z);
+    if (!(r >= r_lo && r < r_hi)) continue;
+    double t = floor((r - r_lo) / w);
+    if (!(t >= 0.0 && t < (double)nbins)) continue;
+    counts[(int)t] += 1;
+    charge[(int)t] += s->q[i];
+  }
+  return OR_OK;
+}
+
+int or_radial_profiles(int nbins, double r_lo, double r_hi, const int64_t* counts, const double* charge,
+                       int64_t n_samples, double q_fixed, double* r_mid, double* g, double* r_out, double* Q) {
+  if (nbins < 1 || !(r_hi > r_lo) || n_samples < 1) return OR_EINVAL;
+  const double pi = 3.14159265358979323846;
+  double w = (r_hi - r_lo) / (double)nbins;
+  double total = 0.0, q = q_fixed;
+  for (int k = 0; k < nbins; ++k) {
+    double a = r_lo + k * w, b = r_lo + (k + 1) * w;
+    double vol = 4.0 / 3.0 * pi * (b * b * b - a * a * a);
+    g[k] = ((double)counts[k] / (double)n_samples) / vol; /* mean density of bin k */
+    total += g[k];
+    q += charge[k] / (double)n_samples;
+    r_mid[k] = 0.5 * (a + b);
+    r_out[k] = b;
+    Q[k] = q;
+  }
+  for (int k = 0; k < nbins; ++k) g[k] = total > 0.0 ? g[k] / total : 0.0;
+  return OR_OK;
+}

@@ -165,6 +165,20 @@ int or_ion_energy_grad(or_sys* s, int64_t i, const double x[3], double* U, doubl
 int or_mala_run(or_sys* s, uint64_t seed, uint32_t replica, uint64_t m0, int64_t n_moves, double tau,
                 or_record* recs, int64_t* n_accepted);
 
+/* Radial distribution of the mobile ions (Sec. 4, Fig. 6): for every mobile
+   ion, r = sqrt((x x + y y) + z z) and, when r_lo <= r < r_hi, bin
+   k = floor((r - r_lo) / w), w = (r_hi - r_lo) / nbins (all FP64, this order),
+   counted when 0 <= k < nbins; counts[k] += 1 and charge[k] += q (the arrays
+   are added to, not cleared). */
+int or_radial_counts(const or_sys* s, int nbins, double r_lo, double r_hi, int64_t* counts, double* charge);
+/* RDF g and ICDF Q of Sec. 4 from counts accumulated over n_samples
+   configurations: <N_k> = counts[k] / n_samples, V_k = (4/3) pi (r_{k+1}^3 -
+   r_k^3) with r_k = r_lo + k w; g_k = (<N_k>/V_k) / sum_j (<N_j>/V_j) (the bins
+   normalised to sum one); Q at the outer edge of bin k = q_fixed + sum_{j<=k}
+   charge[j] / n_samples.  r_mid, g, r_out and Q have nbins entries. */
+int or_radial_profiles(int nbins, double r_lo, double r_hi, const int64_t* counts, const double* charge,
+                       int64_t n_samples, double q_fixed, double* r_mid, double* g, double* r_out, double* Q);
+
 /* Tree export: one row per node (depth, key, is_leaf, count); leaf members are
    written consecutively into members (sorted ascending) in node order.  Returns
    the number of nodes, or -1 if a buffer is too small. */

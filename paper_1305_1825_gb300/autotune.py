@@ -1,5 +1,7 @@
 """Autotuner of the batched treecode Monte Carlo: leaf capacity C, warps per
-move and the FP32 moment layout (AoS/SoA).
+move and the FP32 moment layout (AoS/SoA); and the minimum expansion number
+N_0 as a function of the order p (Sec. 3.2: clusters with fewer than N_0
+charges are summed directly; Sec. 4 chooses N_0(p) from measured times).
 
 Every candidate runs short persistent batched launches on a subset of the
 replicas (CUDA-event timing).  Because C changes the tree and therefore the
@@ -58,14 +60,15 @@ def accuracy(systems, n_moves=40, seed=0, reps=4):
 def time_batch(systems, seeds, warps, layout, moves=200, launches=3):
     import torch
     batch = bhmc.Batch(systems, warps=warps, layout=layout)
-    batch.step_mc(moves // 4, 1.0, seeds)  # warm-up
+    step = systems[0].get("step", 1.0)
+    batch.step_mc(moves // 4, step, seeds)  # warm-up
     move0 = moves // 4
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(launches):
-        batch.step_mc(moves, 1.0, seeds, move0=move0)
+        batch.step_mc(moves, step, seeds, move0=move0)
         move0 += moves
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -95,3 +98,32 @@ def autotune(systems, seeds, C_values=(4, 8, 16, 32), warps_values=(1, 2, 4, 8),
     ok = [r for r in results if acc[r["C"]]["E"] <= bound]
     best = max(ok or results, key=lambda r: r["moves_per_s"])
     return {"best": best, "results": results, "accuracy": acc, "accuracy_bound_E": bound}
+
+
+def _with(systems, **kw):
+    out = []
+    for wl in systems:
+        w = dict(wl)
+        w["params"] = dict(wl["params"], **kw)
+        out.append(w)
+    return out
+
+
+def tune_n0(systems, seeds, p_values=tuple(range(11)), n0_values=(0, 2, 4, 8, 16, 32), warps=8,
+            layout=bhmc.LAYOUT_AOS, moves=400, tol=0.02, verbose=False):
+    """N_0(p) by timing: for each order p the batched moves/s of every N_0, and
+    the chosen N_0, the smallest whose rate is within `tol` of the fastest
+    (a larger N_0 only adds direct terms, so it never costs accuracy).
+    Returns {p: {"chosen": N_0, "rates": {N_0: moves/s}}}."""
+    out = {}
+    for p in p_values:
+        rates = {}
+        for n0 in n0_values:
+            rates[n0] = time_batch(_with(systems, p=p, N0=n0), seeds, warps, layout, moves=moves)
+            if verbose:
+                print({"p": p, "N0": n0, "moves_per_s": rates[n0]}, flush=True)
+        top = max(rates.values())
+        chosen = min(n0 for n0, r in rates.items() if r >= (1.0 - tol) * top)
+        out[p] = {"chosen": chosen, "rates": rates}
+    return out
+

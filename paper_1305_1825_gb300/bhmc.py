@@ -91,6 +91,12 @@ def lib():
         L.bhmc_energy_counters.argtypes = [C.c_void_p, _dp, C.POINTER(Counters)]
         L.bhmc_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
         L.bhmc_batch_radial_counts.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
+        L.bhmc_set_radial_sampling.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int64]
+        L.bhmc_get_radial_samples.argtypes = [C.c_void_p, _i64p, _dp, _i64p]
+        L.bhmc_batch_set_radial_sampling.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int64]
+        L.bhmc_batch_get_radial_samples.argtypes = [C.c_void_p, _i64p, _dp, _i64p]
+        L.bhmc_radial_profiles.argtypes = [C.c_int32, C.c_double, C.c_double, _i64p, _dp, C.c_int64, C.c_double,
+                                           _dp, _dp, _dp, _dp]
         L.bhmc_step_mala.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_uint64, C.c_uint64,
                                      C.POINTER(McStats), C.c_void_p]
         L.bhmc_get_energy.argtypes = [C.c_void_p, _dp]
@@ -257,18 +263,33 @@ def bhmc_radial_counts(h, counts, charge, r_lo, r_hi, batch=False):
 
 
 def radial_profiles(counts, charge, r_lo, r_hi, samples, q_fixed=0.0):
-    """RDF and ICDF of Sec. 4 from accumulated radial counts: with <N_k> the
-    mean count of bin k (counts / samples) and V_k its shell volume,
-    g_k = (<N_k> / V_k) / sum_j (<N_j> / V_j) (the bins normalised to sum 1),
-    Q(r_k) = q_fixed + sum_{j <= k} <q N_j> at the outer edge r_k of bin k.
-    Returns (bin centres, g, outer edges, Q)."""
+    """(bin centres, g, outer edges, Q) of Sec. 4 from accumulated radial counts
+    (bhmc_radial_profiles)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    charge = np.ascontiguousarray(charge, dtype=np.float64)
     n = len(counts)
-    edges = np.linspace(r_lo, r_hi, n + 1)
-    vol = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
-    rho = counts / float(samples) / vol
-    g = rho / rho.sum()
-    Q = q_fixed + np.cumsum(charge / float(samples))
-    return 0.5 * (edges[1:] + edges[:-1]), g, edges[1:], Q
+    out = [np.zeros(n) for _ in range(4)]
+    _check(lib().bhmc_radial_profiles(n, r_lo, r_hi, counts.ctypes.data_as(_i64p), charge.ctypes.data_as(_dp),
+                                      int(samples), q_fixed, *[o.ctypes.data_as(_dp) for o in out]),
+           "bhmc_radial_profiles")
+    return tuple(out)
+
+
+def bhmc_set_radial_sampling(h, nbins, r_lo, r_hi, every, batch=False):
+    f = lib().bhmc_batch_set_radial_sampling if batch else lib().bhmc_set_radial_sampling
+    _check(f(h, nbins, r_lo, r_hi, every), "bhmc_set_radial_sampling")
+
+
+def bhmc_get_radial_samples(h, nbins, n_rep=None):
+    """(counts, charge, n_samples); with n_rep, per replica arrays [n_rep, nbins]."""
+    shape = (nbins,) if n_rep is None else (n_rep, nbins)
+    counts = np.zeros(shape, dtype=np.int64)
+    charge = np.zeros(shape)
+    ns = np.zeros(1 if n_rep is None else n_rep, dtype=np.int64)
+    f = lib().bhmc_get_radial_samples if n_rep is None else lib().bhmc_batch_get_radial_samples
+    _check(f(h, counts.ctypes.data_as(_i64p), charge.ctypes.data_as(_dp), ns.ctypes.data_as(_i64p)),
+           "bhmc_get_radial_samples")
+    return counts, charge, (int(ns[0]) if n_rep is None else ns)
 
 
 def bhmc_energy_direct(h):
@@ -471,6 +492,13 @@ class Context:
     def radial_counts(self, counts, charge, r_lo, r_hi):
         bhmc_radial_counts(self.h, counts, charge, r_lo, r_hi)
 
+    def set_radial_sampling(self, nbins, r_lo, r_hi, every):
+        self._rdf_nbins = nbins
+        bhmc_set_radial_sampling(self.h, nbins, r_lo, r_hi, every)
+
+    def radial_samples(self):
+        return bhmc_get_radial_samples(self.h, self._rdf_nbins)
+
     def energy_direct(self):
         return bhmc_energy_direct(self.h)
 
@@ -528,6 +556,14 @@ class Batch:
 
     def radial_counts(self, counts, charge, r_lo, r_hi):
         bhmc_radial_counts(self.h, counts, charge, r_lo, r_hi, batch=True)
+
+    def set_radial_sampling(self, nbins, r_lo, r_hi, every):
+        self._rdf_nbins = nbins
+        bhmc_set_radial_sampling(self.h, nbins, r_lo, r_hi, every, batch=True)
+
+    def radial_samples(self):
+        """(counts [n_rep, nbins], charge [n_rep, nbins], n_samples [n_rep])."""
+        return bhmc_get_radial_samples(self.h, self._rdf_nbins, n_rep=self.n)
 
     def close(self):
         if self.h:

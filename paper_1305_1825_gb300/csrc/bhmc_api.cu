@@ -40,6 +40,7 @@ struct bhmc_ctx {
   bool borrowed = false;
   bool w_stale = true;  // W32 not refreshed since the moments last changed
   bhmc_counters last = {0, 0, 0, 0};  // counters of the last delta_energy / energy_counters
+  void* rdf_buf = nullptr;            // radial sampling: running histogram and accumulators
 };
 
 struct bhmc_batch {
@@ -487,7 +488,61 @@ static void ctx_free(bhmc_ctx* c) {
   cudaFree(c->arena);
   cudaFree(c->io);
   cudaFreeHost(c->io_host);
+  cudaFree(c->rdf_buf);
   delete c;
+}
+
+// Radial sampling of a context (see bhmc_set_radial_sampling): buffers, the
+// running histogram of the current configuration, zeroed accumulators.
+static bhmc_status rdf_setup(bhmc_ctx* c, int32_t nbins, double r_lo, double r_hi, int64_t every) {
+  bhmc_status rc = ctx_check(c);
+  if (rc != BHMC_OK) return rc;
+  if (nbins < 0 || nbins > (1 << 20) || every < 0) return BHMC_EINVAL;
+  SysDev& S = c->S;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return BHMC_ECUDA;
+  cudaFree(c->rdf_buf);
+  c->rdf_buf = nullptr;
+  S.rdf_nbins = 0;
+  S.rdf_every = 0;
+  S.rdf_run = S.rdf_acc = S.rdf_nsamp = nullptr;
+  S.rdf_runq = S.rdf_accq = nullptr;
+  if (nbins == 0) return BHMC_OK;
+  if (!(r_hi > r_lo) || !std::isfinite(r_lo) || !std::isfinite(r_hi)) return BHMC_EINVAL;
+  const size_t bytes = sizeof(unsigned long long) * (4 * (size_t)nbins + 1);
+  if (cudaMalloc(&c->rdf_buf, bytes) != cudaSuccess) return BHMC_ENOMEM;
+  char* b = static_cast<char*>(c->rdf_buf);
+  const size_t nb = sizeof(unsigned long long) * (size_t)nbins;
+  S.rdf_run = reinterpret_cast<unsigned long long*>(b);
+  S.rdf_runq = reinterpret_cast<double*>(b + nb);
+  S.rdf_acc = reinterpret_cast<unsigned long long*>(b + 2 * nb);
+  S.rdf_accq = reinterpret_cast<double*>(b + 3 * nb);
+  S.rdf_nsamp = reinterpret_cast<unsigned long long*>(b + 4 * nb);
+  S.rdf_lo = r_lo;
+  S.rdf_hi = r_hi;
+  S.rdf_w = (r_hi - r_lo) / (double)nbins;
+  if (cudaMemsetAsync(c->rdf_buf, 0, bytes, c->stream) != cudaSuccess ||
+      launch_radial_counts(S, nbins, r_lo, r_hi, S.rdf_w, S.rdf_run, S.rdf_runq, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return BHMC_ECUDA;
+  S.rdf_nbins = nbins;
+  S.rdf_every = every;
+  return BHMC_OK;
+}
+
+static bhmc_status rdf_read(bhmc_ctx* c, int64_t* counts, double* charge, int64_t* n_samples) {
+  bhmc_status rc = ctx_check(c);
+  if (rc != BHMC_OK) return rc;
+  const SysDev& S = c->S;
+  if (S.rdf_nbins <= 0) return BHMC_ESTATE;
+  const int nb = S.rdf_nbins;
+  std::vector<unsigned long long> hc(nb), hn(1);
+  CK(cudaMemcpyAsync(hc.data(), S.rdf_acc, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(charge, S.rdf_accq, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hn.data(), S.rdf_nsamp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < nb; ++k) counts[k] = (int64_t)hc[k];
+  *n_samples = (int64_t)hn[0];
+  return BHMC_OK;
 }
 
 static bhmc_status ctx_make(const bhmc_params* P, int64_t n_mob, int64_t n_fix, const double* q,
@@ -760,6 +815,37 @@ static bhmc_status radial_impl(bhmc_ctx* const* ctxs, int n, int32_t nbins, doub
 bhmc_status bhmc_radial_counts(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t* counts,
                                double* charge) {
   return radial_impl(&ctx, 1, nbins, r_lo, r_hi, counts, charge);
+}
+
+bhmc_status bhmc_set_radial_sampling(bhmc_ctx* ctx, int32_t nbins, double r_lo, double r_hi, int64_t every) {
+  if (ctx && ctx->borrowed) return BHMC_EINVAL;  // a replica: use bhmc_batch_set_radial_sampling
+  return rdf_setup(ctx, nbins, r_lo, r_hi, every);
+}
+
+bhmc_status bhmc_get_radial_samples(bhmc_ctx* ctx, int64_t* counts, double* charge, int64_t* n_samples) {
+  if (!counts || !charge || !n_samples) return BHMC_EINVAL;
+  return rdf_read(ctx, counts, charge, n_samples);
+}
+
+bhmc_status bhmc_radial_profiles(int32_t nbins, double r_lo, double r_hi, const int64_t* counts,
+                                 const double* charge, int64_t n_samples, double q_fixed, double* r_mid, double* g,
+                                 double* r_out, double* Q) {
+  if (nbins < 1 || !(r_hi > r_lo) || n_samples < 1 || !counts || !charge || !r_mid || !g || !r_out || !Q)
+    return BHMC_EINVAL;
+  const double w = (r_hi - r_lo) / (double)nbins;
+  double total = 0.0, q = q_fixed;
+  for (int k = 0; k < nbins; ++k) {
+    const double a = r_lo + k * w, b = r_lo + (k + 1) * w;
+    const double vol = 4.0 / 3.0 * 3.14159265358979323846 * (b * b * b - a * a * a);
+    g[k] = ((double)counts[k] / (double)n_samples) / vol;  // mean number density of the bin
+    total += g[k];
+    q += charge[k] / (double)n_samples;
+    r_mid[k] = 0.5 * (a + b);
+    r_out[k] = b;
+    Q[k] = q;
+  }
+  for (int k = 0; k < nbins; ++k) g[k] = total > 0.0 ? g[k] / total : 0.0;
+  return BHMC_OK;
 }
 
 bhmc_status bhmc_get_energy(bhmc_ctx* ctx, double* E) {
@@ -1118,6 +1204,31 @@ bhmc_status bhmc_batch_radial_counts(bhmc_batch* B, int32_t nbins, double r_lo, 
                                      double* charge) {
   if (!B) return BHMC_EINVAL;
   return radial_impl(B->reps.data(), (int)B->reps.size(), nbins, r_lo, r_hi, counts, charge);
+}
+
+bhmc_status bhmc_batch_set_radial_sampling(bhmc_batch* B, int32_t nbins, double r_lo, double r_hi,
+                                           int64_t every) {
+  if (!B) return BHMC_EINVAL;
+  const int n = (int)B->reps.size();
+  std::vector<SysDev> views(n);
+  for (int r = 0; r < n; ++r) {
+    bhmc_status rc = rdf_setup(B->reps[r], nbins, r_lo, r_hi, every);
+    if (rc != BHMC_OK) return rc;
+    views[r] = B->reps[r]->S;
+  }
+  // the batched kernel reads the replicas' device views
+  CK(cudaMemcpy(B->d_views, views.data(), sizeof(SysDev) * n, cudaMemcpyHostToDevice));
+  return BHMC_OK;
+}
+
+bhmc_status bhmc_batch_get_radial_samples(bhmc_batch* B, int64_t* counts, double* charge, int64_t* n_samples) {
+  if (!B || !counts || !charge || !n_samples) return BHMC_EINVAL;
+  for (size_t r = 0; r < B->reps.size(); ++r) {
+    const int nb = B->reps[r]->S.rdf_nbins;
+    bhmc_status rc = rdf_read(B->reps[r], counts + r * (size_t)nb, charge + r * (size_t)nb, n_samples + r);
+    if (rc != BHMC_OK) return rc;
+  }
+  return BHMC_OK;
 }
 
 }  // extern "C"

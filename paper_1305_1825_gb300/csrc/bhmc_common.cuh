@@ -78,6 +78,18 @@ struct SysDev {
   // state
   double* energy;
   int* err;
+  // Radial sampling of the mobile ions during the chains (Sec. 4, Fig. 6;
+  // rdf_nbins = 0: off): a running histogram of the current configuration,
+  // kept by every committed move, is added to the accumulators after every
+  // rdf_every-th move (absolute move index).
+  int rdf_nbins;
+  long long rdf_every;
+  double rdf_lo, rdf_hi, rdf_w;
+  unsigned long long* rdf_run;   // [nbins] current counts
+  double* rdf_runq;              // [nbins] current charge
+  unsigned long long* rdf_acc;   // [nbins] summed over the samples
+  double* rdf_accq;              // [nbins]
+  unsigned long long* rdf_nsamp; // [1]
 };
 
 struct MoveRec;
@@ -228,6 +240,35 @@ __device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S
 // Charge j is a fixed charge held outside the tree (fixed_direct).
 __host__ __device__ __forceinline__ bool off_tree(const SysDev& S, int j) {
   return S.fixed_direct && j >= S.n_mob && j < S.n_mob + S.n_fix;
+}
+
+// Radial bin of a mobile ion at squared radius r2 (Sec. 4 RDF): r =
+// sqrt(r2), k = floor((r - lo) / w) in FP64, -1 outside [lo, hi) or the bins.
+__device__ __forceinline__ int rdf_bin(const SysDev& S, double r2) {
+  const double r = __dsqrt_rn(r2);
+  if (!(r >= S.rdf_lo && r < S.rdf_hi)) return -1;
+  const double t = floor(__ddiv_rn(__dsub_rn(r, S.rdf_lo), S.rdf_w));
+  return (t >= 0.0 && t < (double)S.rdf_nbins) ? (int)t : -1;
+}
+
+// Adds the running histogram to the accumulators `times` times (the samples
+// of that many sample points taken in the same configuration); threads of
+// the calling block share the bins.
+__device__ __forceinline__ void rdf_sample(const SysDev& S, unsigned long long times) {
+  if (!times) return;
+  for (int k = threadIdx.x; k < S.rdf_nbins; k += blockDim.x) {
+    S.rdf_acc[k] += times * S.rdf_run[k];
+    S.rdf_accq[k] += (double)times * S.rdf_runq[k];
+  }
+  if (threadIdx.x == 0) *S.rdf_nsamp += times;
+}
+
+// Sample points among the moves [m0, m1): moves m with (m + 1) % every == 0.
+__device__ __forceinline__ unsigned long long rdf_points(const SysDev& S, unsigned long long m0,
+                                                         unsigned long long m1) {
+  if (S.rdf_nbins <= 0 || S.rdf_every <= 0 || m1 <= m0) return 0ULL;
+  const unsigned long long e = (unsigned long long)S.rdf_every;
+  return m1 / e - m0 / e;
 }
 
 // Exact potential sum_f q_f / |r_f - x| at x of the fixed charges held outside

@@ -23,6 +23,7 @@ struct MoveSetup {
   int rej_dom, rej_shell, rej_img;
   double dE, alpha;
   double fix;  // sum over the points of weight x exact potential of the off-tree fixed charges
+  int bin_a, bin_b;  // radial bins of the ion's old and new position (radial sampling on)
 };
 
 struct MoveSh : MoveSetup {
@@ -144,6 +145,11 @@ static __device__ void setup_roles(const SysDev& S, MoveSetup& sh, int wb) {
       const double bk = sh.b[k];
       const unsigned long long kb = lane_key(S, bk, k, base, m3);
       const double r2 = lane_r2(bk, base, m3);
+      if (S.rdf_nbins > 0) {  // radial bins of the old (lane 1) and new (lane 0) position
+        const double r2a = lane_r2(__longlong_as_double((long long)val), base, m3);
+        if (k == 0) sh.bin_b = rdf_bin(S, r2);
+        if (k == 1) sh.bin_a = rdf_bin(S, r2a);
+      }
       if (k == 0) {
         T.pkey[1] = kb;
         sh.rej_dom = kb == 0ULL;  // outside the root cube
@@ -501,6 +507,16 @@ static __device__ void move_slots(const SysDev& S, MoveSh& sh) {
     S.pz[j] = B_[2];
     S.pq[j] = qb;
     S.ckey[j] = sh.T.pkey[pb];
+  }
+  if (S.rdf_nbins > 0) {  // the running radial histogram follows the moved ion
+    if (sh.bin_a >= 0) {
+      S.rdf_run[sh.bin_a] -= 1ULL;
+      S.rdf_runq[sh.bin_a] -= sh.q;
+    }
+    if (sh.bin_b >= 0) {
+      S.rdf_run[sh.bin_b] += 1ULL;
+      S.rdf_runq[sh.bin_b] += sh.q;
+    }
   }
 }
 
@@ -1090,6 +1106,7 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step(SysDev S, unsigned
     tally(stats, o, st.sh.flagged);
     stats->energy = *S.energy;
   }
+  if (o >= 0) rdf_sample(S, rdf_points(S, m, m + 1));
 }
 
 template <int P, typename Real, int LAYOUT>
@@ -1103,6 +1120,7 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step_mala(SysDev S, uns
     tally(stats, o, st.sh.flagged);
     stats->energy = *S.energy;
   }
+  if (o >= 0) rdf_sample(S, rdf_points(S, m, m + 1));
 }
 
 
@@ -1181,6 +1199,7 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
                                              t + 1 < args->n_moves);
       if (o < 0) break;
       if (threadIdx.x == 0) tally(&loc, o, st.sh.flagged);
+      rdf_sample(S, rdf_points(S, args->move0 + t, args->move0 + t + 1));
     }
     if (threadIdx.x == 0) {
       loc.energy = *S.energy;
@@ -1325,6 +1344,14 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
     }
     __syncthreads();
     const int first = plan[0], nfin = plan[1], bad = plan[2];
+    // radial samples of the moves made final before the accepted one (or of
+    // all of them) see the tree before the commit: taken by the committing
+    // CTA (or CTA 0) before it commits
+    const unsigned long long m_step = move0 + done;
+    if (!bad && S.rdf_nbins > 0 && (int)rank == (first < (int)K ? first : 0)) {
+      rdf_sample(S, rdf_points(S, m_step, m_step + (unsigned long long)(first < (int)K ? first : nfin)));
+      __syncthreads();
+    }
     // this CTA's trial of the next step, set up while the commit runs (valid
     // unless it draws the ion that the commit moves)
     const unsigned long long mn = move0 + done + (unsigned long long)nfin + rank;
@@ -1372,6 +1399,8 @@ __device__ void spec_chain(const SysDev& S, unsigned long long move0, unsigned l
     __syncthreads();
     cluster_sync_all();  // the tree is final before the next step, and `word` is read
     if (bad) break;
+    if (S.rdf_nbins > 0 && first < (int)K && (int)rank == first)  // the accepted move's own sample
+      rdf_sample(S, rdf_points(S, m_step + (unsigned long long)first, m_step + (unsigned long long)first + 1ULL));
     if (threadIdx.x == 0) {
       plan[3] = first < (int)K ? ld_cluster_int(&cerr, (unsigned)first) : 0;
       // a setup that read the moved ion's old position is redone
