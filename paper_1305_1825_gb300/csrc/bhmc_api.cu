@@ -878,8 +878,9 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
   const int warps = BHMC_ENERGY_WARPS;  // each warp evaluates 32 targets at a time
   int grid = (ctx->S.n_tree + 32 * warps - 1) / (32 * warps);
   grid = std::max(1, std::min(grid, 152 * 16));
-  // one partial per warp, then q_f phi_f of the fixed charges held outside the tree
-  const int n_off = ctx->S.fixed_direct ? ctx->S.n_fix : 0;
+  // one partial per warp, then q_f phi_f of each fixed charge held outside the
+  // tree and sum_j q_j phi_fixed(r_j) over the tree's charges
+  const int n_off = ctx->S.fixed_direct && ctx->S.n_fix > 0 ? ctx->S.n_fix + 1 : 0;
   double* partial = nullptr;
   int* derr = nullptr;  // error flag, then three counters (8-byte aligned)
   if (cudaMalloc(&partial, sizeof(double) * ((size_t)grid * warps + n_off)) != cudaSuccess) return BHMC_ENOMEM;
@@ -909,7 +910,7 @@ static bhmc_status energy_impl(bhmc_ctx* ctx, double* E, double* phi_out, int32_
             dispatch_energy(ctx, grid, partial, dphi, derr, dcnt) == cudaSuccess &&
             (n_off == 0 ||
              (cudaMemsetAsync(qphi, 0, sizeof(double) * n_off, ctx->stream) == cudaSuccess &&
-              (!dphi || cudaMemsetAsync(dphi + ctx->S.n_mob, 0, sizeof(double) * n_off, ctx->stream) == cudaSuccess) &&
+              (!dphi || cudaMemsetAsync(dphi + ctx->S.n_mob, 0, sizeof(double) * ctx->S.n_fix, ctx->stream) == cudaSuccess) &&
               launch_fixed_targets(ctx->S, dphi, qphi, ctx->stream) == cudaSuccess)) &&
             cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                             ctx->stream) == cudaSuccess &&

@@ -469,18 +469,154 @@ cudaError_t launch_forces_push(const SysDev& S, const double* phi, const double*
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fixed charges held outside the tree (fixed_direct).  The traversal kernels
+// of the energy and force passes see only the tree; these kernels add every
+// pair that involves a fixed charge, exactly and in FP64.
+
+// Sum over the block of v (valid in thread 0); every thread calls it.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// Potential at fixed charge f = n_mob + blockIdx.x: the exact sum over every
+// other charge.  Block (f, c) sums chunk c and adds it to phi[f] (phi may be
+// null) and, times q_f, to qphi[blockIdx.x] (both zeroed by the caller).
+__global__ void __launch_bounds__(256) k_fixed_targets(SysDev S, double* phi, double* qphi) {
+  const int f = S.n_mob + blockIdx.x;
+  const double x[3] = {S.px[f], S.py[f], S.pz[f]};
+  double acc = 0.0;
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.y * blockDim.x) {
+    if (j == f) continue;
+    const double e0 = __dsub_rn(S.px[j], x[0]), e1 = __dsub_rn(S.py[j], x[1]), e2 = __dsub_rn(S.pz[j], x[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+    acc += __ddiv_rn(S.pq[j], __dsqrt_rn(r2));
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) {
+    atomicAdd(&qphi[blockIdx.x], S.pq[f] * t);
+    if (phi) atomicAdd(&phi[f], t);
+  }
+}
+
+// The fixed charges' exact potential at every charge of the tree, added to
+// phi[j] (may be null; it holds the traversal's value), and
+// sum_j q_j phi_fixed(r_j) added to *qsum.
+__global__ void __launch_bounds__(256) k_fixed_tree_targets(SysDev S, double* phi, double* qsum) {
+  double acc = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.x * blockDim.x) {
+    if (off_tree(S, j)) continue;
+    const double x[3] = {S.px[j], S.py[j], S.pz[j]};
+    const double v = fixed_phi(S, x, nullptr);
+    if (phi) phi[j] += v;
+    acc += S.pq[j] * v;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(qsum, t);
+}
+
+// Adjoint of the pairs of fixed charge f = n_mob + blockIdx.x with every
+// other charge: block (f, c) takes chunk c; target side phi_f and
+// q_f grad phi_f added to phi[f] and tgrad[f] (zeroed by the caller), source
+// side q_f / r to psi[j] and -q_f q_j (r_j - r_f) / r^3 to src[j].
+__global__ void __launch_bounds__(256) k_forces_fixed(SysDev S, double* phi, double* tgrad, double* psi,
+                                                      double* src) {
+  const int f = S.n_mob + blockIdx.x;
+  const double x[3] = {S.px[f], S.py[f], S.pz[f]};
+  const double qf = S.pq[f];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.y * blockDim.x) {
+    if (j == f) continue;
+    const double e[3] = {__dsub_rn(S.px[j], x[0]), __dsub_rn(S.py[j], x[1]), __dsub_rn(S.pz[j], x[2])};
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+    const double r = __dsqrt_rn(r2), r3 = __dmul_rn(r2, r);
+    const double qj = S.pq[j];
+    a[0] += __ddiv_rn(qj, r);
+    atomicAdd(&psi[j], __ddiv_rn(qf, r));
+    for (int c = 0; c < 3; ++c) {
+      const double t = __ddiv_rn(e[c], r3);
+      a[1 + c] += qj * t;
+      atomicAdd(&src[3 * j + c], -qf * qj * t);
+    }
+  }
+  for (int u = 0; u < 4; ++u) {
+    const double t = block_sum(a[u]);
+    if (threadIdx.x == 0) atomicAdd(u == 0 ? &phi[f] : &tgrad[3 * f + u - 1], u == 0 ? t : qf * t);
+  }
+}
+
+// Adjoint of the pairs of every tree charge j with the fixed charges: target
+// side phi_fixed(r_j) and q_j grad phi_fixed(r_j) added to phi[j] and
+// tgrad[j] (which hold the traversal's values), source side q_j / r and
+// -q_j q_f (r_f - r_j) / r^3 summed over each warp and added to psi[f], src[f].
+__global__ void __launch_bounds__(256) k_forces_fixed_tree(SysDev S, double* phi, double* tgrad, double* psi,
+                                                           double* src) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < S.n_tot; base += stride) {
+    const int j = base + lane;
+    const bool valid = j < S.n_tot && !off_tree(S, j);
+    double x[3] = {0.0, 0.0, 0.0}, qj = 0.0;
+    if (valid) {
+      x[0] = S.px[j];
+      x[1] = S.py[j];
+      x[2] = S.pz[j];
+      qj = S.pq[j];
+      double g[3];
+      phi[j] += fixed_phi(S, x, g);
+      for (int c = 0; c < 3; ++c) tgrad[3 * j + c] += qj * g[c];
+    }
+    for (int f = S.n_mob; f < S.n_mob + S.n_fix; ++f) {
+      double w[4] = {0.0, 0.0, 0.0, 0.0};
+      if (valid) {
+        const double e[3] = {__dsub_rn(S.px[f], x[0]), __dsub_rn(S.py[f], x[1]), __dsub_rn(S.pz[f], x[2])};
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+        const double r = __dsqrt_rn(r2), r3 = __dmul_rn(r2, r);
+        const double qq = __dmul_rn(qj, S.pq[f]);
+        w[0] = __ddiv_rn(qj, r);
+        for (int c = 0; c < 3; ++c) w[1 + c] = -__ddiv_rn(__dmul_rn(qq, e[c]), r3);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] += __shfl_xor_sync(FULL, w[u], o);
+      if (lane == 0) {
+        atomicAdd(&psi[f], w[0]);
+        for (int c = 0; c < 3; ++c) atomicAdd(&src[3 * f + c], w[1 + c]);
+      }
+    }
+  }
+}
+
 // Fixed charges held outside the tree: blocks per fixed charge so that the
 // O(N) exact sums spread over the GPU.
 static inline dim3 fixed_grid(const SysDev& S) {
   return dim3((unsigned)S.n_fix, (unsigned)std::max(1, std::min(64, (S.n_tot + 2047) / 2048)), 1);
 }
+static inline int tree_grid(const SysDev& S) { return std::max(1, std::min(152 * 8, (S.n_tot + 255) / 256)); }
 cudaError_t launch_fixed_targets(const SysDev& S, double* phi, double* qphi, cudaStream_t st) {
-  if (S.fixed_direct && S.n_fix > 0) k_fixed_targets<<<fixed_grid(S), 256, 0, st>>>(S, phi, qphi);
+  if (S.fixed_direct && S.n_fix > 0) {
+    k_fixed_targets<<<fixed_grid(S), 256, 0, st>>>(S, phi, qphi);
+    k_fixed_tree_targets<<<tree_grid(S), 256, 0, st>>>(S, phi, qphi + S.n_fix);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_forces_fixed(const SysDev& S, double* phi, double* tgrad, double* psi, double* src,
                                 cudaStream_t st) {
-  if (S.fixed_direct && S.n_fix > 0) k_forces_fixed<<<fixed_grid(S), 256, 0, st>>>(S, phi, tgrad, psi, src);
+  if (S.fixed_direct && S.n_fix > 0) {
+    k_forces_fixed<<<fixed_grid(S), 256, 0, st>>>(S, phi, tgrad, psi, src);
+    k_forces_fixed_tree<<<tree_grid(S), 256, 0, st>>>(S, phi, tgrad, psi, src);
+  }
   return cudaGetLastError();
 }
 

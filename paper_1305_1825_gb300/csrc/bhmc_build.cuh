@@ -24,9 +24,12 @@ cudaError_t launch_radial_counts(const SysDev& S, int nbins, double lo, double h
 cudaError_t launch_commit(const SysDev& S, int i, const double* b, int* status, cudaStream_t st);
 cudaError_t launch_direct_energy(const SysDev& S, double* partial, int nblk, cudaStream_t st);
 cudaError_t launch_interleave(const SysDev& S, double* q, double* xyz, cudaStream_t st);
-// fixed charges held outside the tree (fixed_direct): exact potential at each
-// fixed charge (phi[f] may be null; phi and qphi accumulate, zeroed by the
-// caller; qphi[f] = q_f phi_f), and the exact pair terms of the adjoint pass
+// fixed charges held outside the tree (fixed_direct): every pair with a fixed
+// charge, exactly.  Energy pass: each fixed charge's potential (phi[f], may be
+// null, zeroed by the caller; qphi[f] = q_f phi_f for f < n_fix) and the
+// fixed charges' potential at every tree charge (added to phi[j];
+// qphi[n_fix] += sum_j q_j phi_fixed(r_j)); qphi zeroed by the caller.  Force
+// pass: the same pairs' target and source terms added to the adjoint arrays.
 cudaError_t launch_fixed_targets(const SysDev& S, double* phi, double* qphi, cudaStream_t st);
 cudaError_t launch_forces_fixed(const SysDev& S, double* phi, double* tgrad, double* psi, double* src,
                                 cudaStream_t st);

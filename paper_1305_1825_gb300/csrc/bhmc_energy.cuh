@@ -214,10 +214,8 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
       __syncwarp();
     }
     if (valid) {
-      // the fixed charges held outside the tree enter exactly (FP64)
-      const double v = acc.value() + (S.fixed_direct ? fixed_phi(S, x, nullptr) : 0.0);
-      wsum += q * v;
-      if (phi) phi[j] = v;
+      wsum += q * acc.value();
+      if (phi) phi[j] = acc.value();
     }
     __syncwarp();
   }
@@ -240,34 +238,6 @@ __global__ void __launch_bounds__(128) k_energy(SysDev S, const int* order, doub
       atomicAdd(cnt + 1, v1);
       atomicAdd(cnt + 2, v2);
     }
-  }
-}
-
-// Potential at the fixed charges held outside the tree (fixed_direct): the
-// exact FP64 sum over every other charge.  Block (f, c) of a grid of n_fix x
-// gridDim.y blocks sums chunk c of the charges for fixed charge n_mob + f and
-// adds it to phi[n_mob + f] (phi may be null) and, times q_f, to qphi[f]; both
-// are zeroed by the caller.
-static __global__ void __launch_bounds__(256) k_fixed_targets(SysDev S, double* phi, double* qphi) {
-  __shared__ double red[8];
-  const int f = S.n_mob + blockIdx.x;
-  const double x[3] = {S.px[f], S.py[f], S.pz[f]};
-  double acc = 0.0;
-  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.y * blockDim.x) {
-    if (j == f) continue;
-    const double e0 = __dsub_rn(S.px[j], x[0]), e1 = __dsub_rn(S.py[j], x[1]), e2 = __dsub_rn(S.pz[j], x[2]);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
-    acc += __ddiv_rn(S.pq[j], __dsqrt_rn(r2));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    atomicAdd(&qphi[blockIdx.x], S.pq[f] * t);
-    if (phi) atomicAdd(&phi[f], t);
   }
 }
 

@@ -241,83 +241,15 @@ __global__ void __launch_bounds__(128) k_forces_traverse(SysDev S, const int* or
       }
       __syncwarp();
     }
-    // the fixed charges held outside the tree: exact pairs (FP64), target side
-    double fp = 0.0, fg[3] = {0.0, 0.0, 0.0};
-    if (S.fixed_direct && valid) fp = fixed_phi(S, x, fg);
     if (valid) {
-      phi_out[i] = phi.value() + fp;
-      tgrad[3 * i + 0] = qi * (g0.value() + fg[0]);
-      tgrad[3 * i + 1] = qi * (g1.value() + fg[1]);
-      tgrad[3 * i + 2] = qi * (g2.value() + fg[2]);
-    }
-    if (S.fixed_direct) {
-      // ... and their source side, q_i / r and -q_i q_f (r_f - r_i) / r^3,
-      // summed over the warp and added once per fixed charge
-      for (int f = S.n_mob; f < S.n_mob + S.n_fix; ++f) {
-        double w[4] = {0.0, 0.0, 0.0, 0.0};
-        if (valid) {
-          const double e[3] = {__dsub_rn(S.px[f], x[0]), __dsub_rn(S.py[f], x[1]), __dsub_rn(S.pz[f], x[2])};
-          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
-          const double r = __dsqrt_rn(r2), r3 = __dmul_rn(r2, r);
-          const double qq = __dmul_rn(qi, S.pq[f]);
-          w[0] = __ddiv_rn(qi, r);
-          for (int c = 0; c < 3; ++c) w[1 + c] = -__ddiv_rn(__dmul_rn(qq, e[c]), r3);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) w[u] += __shfl_xor_sync(FULL, w[u], o);
-        if (lane == 0) {
-          atomicAdd(&psi[f], w[0]);
-          for (int c = 0; c < 3; ++c) atomicAdd(&src[3 * f + c], w[1 + c]);
-        }
-      }
+      phi_out[i] = phi.value();
+      tgrad[3 * i + 0] = qi * g0.value();
+      tgrad[3 * i + 1] = qi * g1.value();
+      tgrad[3 * i + 2] = qi * g2.value();
     }
     __syncwarp();
   }
   if (lane == 0 && errv) atomicCAS(err, 0, errv);
-}
-
-// Fixed charges held outside the tree (fixed_direct): exact pairs with every
-// other charge.  Block (f, c) takes chunk c of the charges for fixed charge
-// n_mob + f: target side phi_f and q_f grad phi_f added to phi[f] and tgrad[f]
-// (zeroed by the caller), source side q_f / r to psi[j] and
-// -q_f q_j (r_j - r_f) / r^3 to src[j].
-static __global__ void __launch_bounds__(256) k_forces_fixed(SysDev S, double* phi, double* tgrad, double* psi,
-                                                             double* src) {
-  __shared__ double red[8][4];
-  const int f = S.n_mob + blockIdx.x;
-  const double x[3] = {S.px[f], S.py[f], S.pz[f]};
-  const double qf = S.pq[f];
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < S.n_tot; j += gridDim.y * blockDim.x) {
-    if (j == f) continue;
-    const double e[3] = {__dsub_rn(S.px[j], x[0]), __dsub_rn(S.py[j], x[1]), __dsub_rn(S.pz[j], x[2])};
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
-    const double r = __dsqrt_rn(r2), r3 = __dmul_rn(r2, r);
-    const double qj = S.pq[j];
-    a[0] += __ddiv_rn(qj, r);
-    atomicAdd(&psi[j], __ddiv_rn(qf, r));
-    for (int c = 0; c < 3; ++c) {
-      const double t = __ddiv_rn(e[c], r3);
-      a[1 + c] += qj * t;
-      atomicAdd(&src[3 * j + c], -qf * qj * t);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] += __shfl_xor_sync(0xffffffffu, a[u], o);
-  if ((threadIdx.x & 31) == 0)
-    for (int u = 0; u < 4; ++u) red[threadIdx.x >> 5][u] = a[u];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      for (int u = 0; u < 4; ++u) t[u] += red[w][u];
-    atomicAdd(&phi[f], t[0]);
-    for (int c = 0; c < 3; ++c) atomicAdd(&tgrad[3 * f + c], qf * t[1 + c]);
-  }
 }
 
 // Pass 2: one thread per charge, clusters from the root down to its leaf.
