@@ -49,9 +49,22 @@ struct BlockStore {
   uint2 di[32 * BHMC_MAX_WARPS];         // {leaf, count << 4 | point mask}
   int wcnt[BHMC_MAX_WARPS][3];
   double wsum[BHMC_MAX_WARPS];
+  float wsf[BHMC_MAX_WARPS][2];
   int wred[BHMC_MAX_WARPS][6];
   double wg[BHMC_MAX_WARPS][8];
 };
+
+// h + l += h2 + l2 for unevaluated pairs of floats (Knuth's two-sum of the
+// high parts, the low parts carried): about 44 significant bits, from FP32
+// arithmetic alone.
+__device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
+  const float s = __fadd_rn(h, h2);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  const float t = __fadd_rn(e, __fadd_rn(l, l2));
+  h = __fadd_rn(s, t);
+  l = __fsub_rn(t, __fsub_rn(h, s));
+}
 
 // `path` (may be null) receives per point and level the cluster containing the
 // point; `leafcnt[s]` the count of point s's leaf when the traversal reaches it.
@@ -334,33 +347,50 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     npop = npop_n;
   }
   __syncthreads();
-  // block reductions (result valid in thread 0)
-  double v = acc.value();
+  // block reductions (result valid in thread 0).  The FP32 traversal's
+  // compensated sums are added as float pairs, in FP32 arithmetic, which on
+  // this part issues far faster than FP64; the FP64 traversal's and the
+  // gradient sums are added in FP64.
+  constexpr bool PAIRS = sizeof(Real) == 4 && !GRAD;
+  if constexpr (PAIRS) {
+    float h, l;
+    acc.pair(h, l);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  double gg[8];
-  if (GRAD) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      gg[4 * r] = ga.phi[r].value();
-#pragma unroll
-      for (int c = 0; c < 3; ++c) gg[4 * r + 1 + c] = (double)ga.g[r][c];
+    for (int o = 16; o > 0; o >>= 1) df_add(h, l, __shfl_xor_sync(FULL, h, o), __shfl_xor_sync(FULL, l, o));
+    if (lane == 0) {
+      B.wsf[warp][0] = h;
+      B.wsf[warp][1] = l;
     }
+  } else {
+    double v = acc.value();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    double gg[8];
+    if (GRAD) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) gg[u] += __shfl_xor_sync(FULL, gg[u], o);
+      for (int r = 0; r < 2; ++r) {
+        gg[4 * r] = ga.phi[r].value();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gg[4 * r + 1 + c] = (double)ga.g[r][c];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gg[u] += __shfl_xor_sync(FULL, gg[u], o);
+    }
+    if (lane == 0) {
+      B.wsum[warp] = v;
+      if (GRAD) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) B.wg[warp][u] = gg[u];
+      }
+    }
   }
   const int r0 = __reduce_add_sync(FULL, visited), r1 = __reduce_add_sync(FULL, accepted);
   const int r2 = __reduce_add_sync(FULL, pairs), r3 = __reduce_add_sync(FULL, fp64);
   const int r4 = __reduce_max_sync(FULL, err);
   const int r5 = __any_sync(FULL, ovl) ? 1 : 0;
   if (lane == 0) {
-    B.wsum[warp] = v;
-    if (GRAD) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) B.wg[warp][u] = gg[u];
-    }
     B.wred[warp][0] = r0;
     B.wred[warp][1] = r1;
     B.wred[warp][2] = r2;
@@ -369,26 +399,44 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     B.wred[warp][5] = r5;
   }
   __syncthreads();
-  if (tid == 0) {
-    out.sum = 0.0;
-    for (int r = 0; r < 2; ++r) {
-      out.phi[r] = 0.0;
-      out.grad[r][0] = out.grad[r][1] = out.grad[r][2] = 0.0;
+  // warp 0 adds the per-warp results, one warp per lane
+  if (warp == 0) {
+    const bool in = lane < NW;
+    const int c0 = __reduce_add_sync(FULL, in ? B.wred[lane][0] : 0);
+    const int c1 = __reduce_add_sync(FULL, in ? B.wred[lane][1] : 0);
+    const int c2 = __reduce_add_sync(FULL, in ? B.wred[lane][2] : 0);
+    const int c3 = __reduce_add_sync(FULL, in ? B.wred[lane][3] : 0);
+    const int c4 = __reduce_max_sync(FULL, in ? B.wred[lane][4] : 0);
+    const unsigned c5 = __reduce_or_sync(FULL, in ? (unsigned)B.wred[lane][5] : 0u);
+    double sum = 0.0;
+    if constexpr (PAIRS) {
+      float h = in ? B.wsf[lane][0] : 0.f, l = in ? B.wsf[lane][1] : 0.f;
+#pragma unroll
+      for (int o = BHMC_MAX_WARPS / 2; o > 0; o >>= 1)
+        df_add(h, l, __shfl_xor_sync(FULL, h, o), __shfl_xor_sync(FULL, l, o));
+      if (lane == 0) sum = (double)h + (double)l;
     }
-    out.visited = out.accepted = out.pairs = out.fp64 = out.err = out.overlap = 0;
-    for (int w = 0; w < NW; ++w) {
-      out.sum += B.wsum[w];
-      if (GRAD)
-        for (int r = 0; r < 2; ++r) {
-          out.phi[r] += B.wg[w][4 * r];
-          for (int c = 0; c < 3; ++c) out.grad[r][c] += B.wg[w][4 * r + 1 + c];
+    if (lane == 0) {
+      out.sum = sum;
+      for (int r = 0; r < 2; ++r) {
+        out.phi[r] = 0.0;
+        out.grad[r][0] = out.grad[r][1] = out.grad[r][2] = 0.0;
+      }
+      if (!PAIRS)
+        for (int w = 0; w < NW; ++w) {
+          out.sum += B.wsum[w];
+          if (GRAD)
+            for (int r = 0; r < 2; ++r) {
+              out.phi[r] += B.wg[w][4 * r];
+              for (int c = 0; c < 3; ++c) out.grad[r][c] += B.wg[w][4 * r + 1 + c];
+            }
         }
-      out.visited += B.wred[w][0];
-      out.accepted += B.wred[w][1];
-      out.pairs += B.wred[w][2];
-      out.fp64 += B.wred[w][3];
-      out.overlap |= B.wred[w][5];
-      out.err = max(out.err, B.wred[w][4]);
+      out.visited = c0;
+      out.accepted = c1;
+      out.pairs = c2;
+      out.fp64 = c3;
+      out.err = c4;
+      out.overlap = (int)c5;
     }
   }
 }

@@ -22,7 +22,10 @@ struct MoveSetup {
   int outcome, flagged;
   int rej_dom, rej_shell, rej_img;
   double dE, alpha;
-  double fix;  // sum over the points of weight x exact potential of the off-tree fixed charges
+  float la;    // log(alpha) in FP32, for the Metropolis decision's fast path
+  // the move's exact terms, formed in the setup: weight x potential of the
+  // off-tree fixed charges at every point, plus the ion-image pair terms
+  double fix;
   int bin_a, bin_b;  // radial bins of the ion's old and new position (radial sampling on)
 };
 
@@ -121,6 +124,7 @@ __device__ __forceinline__ void propose(const SysDev& S, MoveSetup& sh, unsigned
     }
   } else {
     sh.alpha = __ll2double_rn(2LL * (long long)u.x + 1LL) * 0x1p-33;  // (u + 1/2) 2^-32 exactly
+    sh.la = logf((float)sh.alpha);
   }
 }
 
@@ -293,7 +297,35 @@ static __device__ void setup_finish(const SysDev& S, MoveSetup& sh, int wb) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fx += __shfl_xor_sync(0xffffffffu, fx, o);
   }
-  if (lane == 0) sh.fix = fx;
+  __syncwarp();
+  if (lane == 0) {
+    // ion-image pair terms q q'/|r - r'| at the new and old positions (in the
+    // traversal's precision), formed here so that the move's decision waits
+    // for none of this arithmetic
+    double pair = 0.0;
+    if (np == 4 && !(sh.rej_dom || sh.rej_shell || sh.rej_img)) {
+      double pb, pa;
+      if (S.prec == BHMC_PREC_F32) {
+        float dx = (T.hi[1][0] - T.hi[3][0]) + (T.lo[1][0] - T.lo[3][0]);
+        float dy = (T.hi[1][1] - T.hi[3][1]) + (T.lo[1][1] - T.lo[3][1]);
+        float dz = (T.hi[1][2] - T.hi[3][2]) + (T.lo[1][2] - T.lo[3][2]);
+        pb = (double)((float)(sh.q * sh.qb_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
+        dx = (T.hi[0][0] - T.hi[2][0]) + (T.lo[0][0] - T.lo[2][0]);
+        dy = (T.hi[0][1] - T.hi[2][1]) + (T.lo[0][1] - T.lo[2][1]);
+        dz = (T.hi[0][2] - T.hi[2][2]) + (T.lo[0][2] - T.lo[2][2]);
+        pa = (double)((float)(sh.q * sh.qa_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
+      } else {
+        double dx = sh.b[0] - sh.bi[0], dy = sh.b[1] - sh.bi[1], dz = sh.b[2] - sh.bi[2];
+        pb = sh.q * sh.qb_img / sqrt(dx * dx + dy * dy + dz * dz);
+        dx = sh.a[0] - sh.ai[0];
+        dy = sh.a[1] - sh.ai[1];
+        dz = sh.a[2] - sh.ai[2];
+        pa = sh.q * sh.qa_img / sqrt(dx * dx + dy * dy + dz * dz);
+      }
+      pair = pb - pa;
+    }
+    sh.fix = fx + pair;
+  }
 }
 
 static __device__ void setup_move(const SysDev& S, MoveSetup& sh) {
@@ -314,35 +346,12 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
   block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr,
                                   sh.leafcnt, o);
   if (threadIdx.x == 0) {
-    double s = o.sum + sh.fix;
+    const double s = o.sum + sh.fix;  // the traversal's sum and the setup's exact terms
     sh.cnt[0][0] = o.visited;
     sh.cnt[0][1] = o.accepted;
     sh.cnt[0][2] = o.pairs;
     sh.cnt[0][3] = o.fp64;
     sh.cnt[0][4] = o.err;
-    if (sh.npts == 4) {
-      // ion-image pair terms q q'/|r - r'| at the new and old positions
-      const TravPts& T = sh.T;
-      double pb, pa;
-      if (sizeof(Real) == 4) {
-        float dx = (T.hi[1][0] - T.hi[3][0]) + (T.lo[1][0] - T.lo[3][0]);
-        float dy = (T.hi[1][1] - T.hi[3][1]) + (T.lo[1][1] - T.lo[3][1]);
-        float dz = (T.hi[1][2] - T.hi[3][2]) + (T.lo[1][2] - T.lo[3][2]);
-        pb = (double)((float)(sh.q * sh.qb_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
-        dx = (T.hi[0][0] - T.hi[2][0]) + (T.lo[0][0] - T.lo[2][0]);
-        dy = (T.hi[0][1] - T.hi[2][1]) + (T.lo[0][1] - T.lo[2][1]);
-        dz = (T.hi[0][2] - T.hi[2][2]) + (T.lo[0][2] - T.lo[2][2]);
-        pa = (double)((float)(sh.q * sh.qa_img) * rsqrtf(dx * dx + dy * dy + dz * dz));
-      } else {
-        double dx = sh.b[0] - sh.bi[0], dy = sh.b[1] - sh.bi[1], dz = sh.b[2] - sh.bi[2];
-        pb = sh.q * sh.qb_img / sqrt(dx * dx + dy * dy + dz * dz);
-        dx = sh.a[0] - sh.ai[0];
-        dy = sh.a[1] - sh.ai[1];
-        dz = sh.a[2] - sh.ai[2];
-        pa = sh.q * sh.qa_img / sqrt(dx * dx + dy * dy + dz * dz);
-      }
-      s += pb - pa;
-    }
     sh.dE = S.lB * s;
     if (o.overlap) {  // hard core (Eq. 2.1): rejected as before evaluation
       sh.outcome = BHMC_REJECT_OVERLAP;
@@ -521,11 +530,15 @@ static __device__ void move_slots(const SysDev& S, MoveSh& sh) {
 }
 
 // Barrier of the first n threads: the whole block (bar 0) or a named barrier.
+// Named barriers use the non-aligned form (threads arrive one by one), which
+// stays correct when a warp reaches it diverged after a lane-dependent branch;
+// the aligned form requires a converged warp, and the compiler does not
+// reconverge warps ahead of inline assembly.
 __device__ __forceinline__ void team_sync(int bar, int n) {
   if (bar == 0)
     __syncthreads();
   else
-    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+    asm volatile("barrier.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
 }
 
 // (A0) of the local adjustment (Sec. 3.3): q (r - r_A)^k, (r - r_A)^k along
@@ -601,9 +614,10 @@ static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int 
   // (A1) FP64 moments per level, both moved charges in one pass: one thread
   // owns each (level, term), the four path clusters of that level (a cluster
   // belongs to one level) are read together, then the ion's update and the
-  // image's are applied in that order (same cluster -> M += mb - ma, else
-  // M_old -= ma and M_new += mb) and each distinct cluster written once.  The
-  // last thread moves the leaf slots meanwhile.
+  // image's are applied in that order (M_old -= ma, M_new += mb; one cluster
+  // may be both) and each distinct cluster written once.  Each update is one
+  // FP64 fused multiply-add of q x^n1 y^n2 by z^n3.  The last thread moves
+  // the leaf slots meanwhile.
   {
     int Dn = 0;
     for (int ps = 0; ps < 2 * sh.nmov; ++ps) Dn = max(Dn, sh.plen[ps] + 1);
@@ -613,7 +627,7 @@ static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int 
       const int d = it / K, t = it - d * K;
       const int n1 = sh.ex[t][0], n2 = sh.ex[t][1], n3 = sh.ex[t][2];
       int a[4];
-      double v[4], mab[4];
+      double v[4], pxy[4], pz[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) a[k] = (k < 2 * sh.nmov && d <= sh.plen[k]) ? sh.path[k][d] : -1;
 #pragma unroll
@@ -621,9 +635,9 @@ static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int 
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int m = k >> 1, side = k & 1;
-        mab[k] = a[k] >= 0 ? __dmul_rn(__dmul_rn(st.pw[m][side][d][0][n1], st.pw[m][side][d][1][n2]),
-                                       st.pw[m][side][d][2][n3])
-                           : 0.0;
+        const bool on = a[k] >= 0;
+        pxy[k] = on ? __dmul_rn(st.pw[m][side][d][0][n1], st.pw[m][side][d][1][n2]) : 0.0;
+        pz[k] = on ? st.pw[m][side][d][2][n3] : 0.0;
       }
       int own[4];
 #pragma unroll
@@ -632,11 +646,12 @@ static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int 
       for (int m = 0; m < 2; ++m) {
         const int ka = 2 * m, kb = 2 * m + 1;
         const bool same = a[ka] >= 0 && a[ka] == a[kb];
-        if (a[ka] >= 0) {  // old cluster: M -= ma, or M += mb - ma when it is also the new one
-          const double x = pick4(v, own[ka]);
-          put4(v, own[ka], same ? __dadd_rn(x, __dsub_rn(mab[kb], mab[ka])) : __dsub_rn(x, mab[ka]));
+        if (a[ka] >= 0) {  // old cluster: M -= ma, then M += mb when it is also the new one
+          double x = __fma_rn(-pxy[ka], pz[ka], pick4(v, own[ka]));
+          if (same) x = __fma_rn(pxy[kb], pz[kb], x);
+          put4(v, own[ka], x);
         }
-        if (a[kb] >= 0 && !same) put4(v, own[kb], __dadd_rn(pick4(v, own[kb]), mab[kb]));
+        if (a[kb] >= 0 && !same) put4(v, own[kb], __fma_rn(pxy[kb], pz[kb], pick4(v, own[kb])));
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -768,10 +783,10 @@ static __device__ void commit_move_block(const SysDev& S, MoveStore& st, int nt 
 // ---------------------------------------------------------------------------
 // Metropolis decision in FP64 (alpha <= exp(-beta dE)), settled in FP32 when
 // the two sides differ by more than a safe margin.
-__device__ __forceinline__ void metropolis(double beta, double dE, double alpha, int& accept,
+__device__ __forceinline__ void metropolis(double beta, double dE, double alpha, float la, int& accept,
                                            int& flagged) {
   const double x = -beta * dE;
-  const float xf = (float)x, la = logf((float)alpha);
+  const float xf = (float)x;
   const float diff = xf - la;
   const float margin = 1e-4f * (1.0f + fabsf(xf) + fabsf(la));
   if (diff > margin) {
@@ -793,8 +808,9 @@ struct MoveRec {
   int outcome, flagged;
 };
 
-// Barrier of warps 5-7 (the lookahead setup of the next move).
-__device__ __forceinline__ void bar_ahead() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+// Barrier of warps 5-7 (the lookahead setup of the next move), non-aligned
+// like team_sync's.
+__device__ __forceinline__ void bar_ahead() { asm volatile("barrier.sync 1, 96;" ::: "memory"); }
 
 // One full trial move m of a chain (all threads).  Returns the outcome, or -1
 // after a device error (recorded in S.err).  With `ahead` (blocks of eight
@@ -845,7 +861,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
       team_sync(bar, nt);
       if (threadIdx.x == 0 && sh.outcome < 0) {
         int acc, fl;
-        metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
+        metropolis(S.beta, sh.dE, sh.alpha, sh.la, acc, fl);
         sh.flagged = fl;
         if (!isfinite(sh.dE)) {
           set_err(S, BHMC_ENONFINITE);
@@ -1281,7 +1297,7 @@ __device__ int spec_eval(const SysDev& S, MoveStore& st, unsigned long long m, u
     __syncthreads();
     if (threadIdx.x == 0 && sh.outcome < 0) {
       int acc, fl;
-      metropolis(S.beta, sh.dE, sh.alpha, acc, fl);
+      metropolis(S.beta, sh.dE, sh.alpha, sh.la, acc, fl);
       sh.flagged = fl;
       if (!isfinite(sh.dE)) {
         set_err(S, BHMC_ENONFINITE);

@@ -344,6 +344,10 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ void pair(float& h, float& l) const {  // value = h + l
+    h = s;
+    l = -c;
+  }
 };
 template <>
 struct Acc<double> {
