@@ -235,7 +235,18 @@ __device__ __forceinline__ bool shell_ok(const SysDev& S, const double x[3]) {
   return r2 >= S.rmin2 && r2 <= S.rmax2;
 }
 
-__device__ __forceinline__ void set_err(const SysDev& S, int code) { atomicCAS(S.err, 0, code); }
+// The running block's copy of its chain's error state (shared memory),
+// raised together with the device error word so that a persistent kernel can
+// test it between moves without a round trip to global memory.  A kernel that
+// reads it first sets it from the error word.
+__device__ __forceinline__ int& block_err() {
+  __shared__ int e;
+  return e;
+}
+__device__ __forceinline__ void set_err(const SysDev& S, int code) {
+  atomicCAS(S.err, 0, code);
+  block_err() = 1;
+}
 
 // Charge j is a fixed charge held outside the tree (fixed_direct).
 __host__ __device__ __forceinline__ bool off_tree(const SysDev& S, int j) {

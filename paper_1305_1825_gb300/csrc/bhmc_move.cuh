@@ -49,6 +49,12 @@ struct MoveSh : MoveSetup {
   MoveSetup nxt;
   unsigned long long nxt_m;
   int moved;  // ion moved by the last move (-1: none), which voids a setup of it
+  double E;   // running FP64 energy of the chain while a kernel holds it
+  // outcome and flag of the last finished move, for reads after its final
+  // barrier: the next move's setup copy may already have overwritten the
+  // MoveSetup fields by then, while these change only after every thread has
+  // passed the next move's first barrier
+  int result, result_flagged;
 };
 
 struct MoveStore {
@@ -334,14 +340,22 @@ static __device__ void setup_move(const SysDev& S, MoveSetup& sh) {
   setup_finish(S, sh, 0);
 }
 
-// All warps: traverse, then thread 0 assembles dE (FP64).  Requires a
-// __syncthreads() after setup.  Returns with sh.dE and sh.cnt filled.
-template <int P, typename Real, int LAYOUT>
-__device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path) {
-  MoveSh& sh = st.sh;
+// Paths and path leaf counts of a move not yet found (all threads).
+__device__ __forceinline__ void clear_paths(MoveSh& sh) {
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
   if (threadIdx.x < 4) sh.leafcnt[threadIdx.x] = -1;
-  __syncthreads();
+}
+
+// All warps: traverse, then thread 0 assembles dE (FP64).  Requires a
+// __syncthreads() after setup (and after clear_paths when init_paths is
+// false).  Returns with sh.dE and sh.cnt filled.
+template <int P, typename Real, int LAYOUT>
+__device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path, bool init_paths = true) {
+  MoveSh& sh = st.sh;
+  if (init_paths) {
+    clear_paths(sh);
+    __syncthreads();
+  }
   TravOut o;
   block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr,
                                   sh.leafcnt, o);
@@ -550,12 +564,19 @@ __device__ __forceinline__ void team_sync(int bar, int n) {
 static __device__ void commit_prep(const SysDev& S, MoveStore& st, int t0, int n) {
   MoveSh& sh = st.sh;
   const int P = S.p;
-  constexpr int NL = BHMC_MAX_D + 1;
   const int tid = (int)threadIdx.x - t0;
   if (tid < 0 || tid >= n) return;
-  for (int it = tid; it < sh.nmov * 2 * NL; it += n) {
-    const int ps = it / NL, d = it - ps * NL;
-    if (d > sh.plen[ps]) continue;
+  // the (path, level) items of the moved charges' paths packed on consecutive
+  // lanes: every warp that holds an item issues the whole FP64 chain, so the
+  // fewer warps hold items, the fewer FP64 instructions the move issues
+  int tot = 0;
+  for (int ps = 0; ps < 2 * sh.nmov; ++ps) tot += sh.plen[ps] + 1;
+  for (int it = tid; it < tot; it += n) {
+    int ps = 0, d = it;
+    while (d > sh.plen[ps]) {
+      d -= sh.plen[ps] + 1;
+      ++ps;
+    }
     const int m = ps >> 1, side = ps & 1;
     const float4 c = S.nA[sh.path[ps][d]];
     const double* X = m ? (side ? sh.bi : sh.ai) : (side ? sh.b : sh.a);
@@ -823,6 +844,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
   MoveSh& sh = st.sh;
   const int warp = threadIdx.x >> 5;
   ahead = ahead && blockDim.x == 256;
+  clear_paths(sh);  // nothing reads the paths before the barrier that ends the setup
   // the look-ahead setup of move m is used unless move m - 1 moved its ion
   // (both read after the barrier that ended move m - 1, so every thread agrees)
   if (sh.nxt_m == m && sh.nxt.i != sh.moved) {
@@ -840,7 +862,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
   __syncthreads();
   if (threadIdx.x == 0) sh.nxt_m = ~0ULL;
   if (sh.outcome < 0) {
-    eval_move<P, Real, LAYOUT>(S, st, true);
+    eval_move<P, Real, LAYOUT>(S, st, true, false);
     if (sh.cnt[0][4]) {
       if (threadIdx.x == 0) set_err(S, sh.cnt[0][4]);
       return -1;
@@ -881,7 +903,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
           team_sync(bar, nt);
         }
         commit_apply(S, st, nt, bar);
-        if (threadIdx.x == 0) *S.energy += sh.dE;
+        if (threadIdx.x == 0) sh.E += sh.dE;
       }
     }
   }
@@ -889,6 +911,8 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
     // not a write of nxt_m here: thread 160 may still be finishing the
     // look-ahead, and its nxt_m = m + 1 must not undo an invalidation
     sh.moved = sh.outcome == BHMC_ACCEPT ? sh.i : -1;
+    sh.result = sh.outcome;
+    sh.result_flagged = sh.flagged;
     if (rec) {
       rec->i = sh.i;
       rec->r[0] = sh.b[0];
@@ -900,7 +924,7 @@ __device__ int mc_move(const SysDev& S, MoveStore& st, unsigned long long m, uns
     }
   }
   __syncthreads();
-  return sh.outcome;
+  return sh.result;
 }
 
 // ---------------------------------------------------------------------------
@@ -1115,12 +1139,16 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS) k_step(SysDev S, unsigned
   __shared__ MoveStore st;
   if (*(volatile int*)S.err) return;
   init_tables(st.sh, S.K);
-  if (threadIdx.x == 0) st.sh.nxt_m = ~0ULL;
+  if (threadIdx.x == 0) {
+    st.sh.nxt_m = ~0ULL;
+    st.sh.E = *S.energy;
+  }
   __syncthreads();
   const int o = mc_move<P, Real, LAYOUT>(S, st, m, replica, key, step, recs, false);
+  if (threadIdx.x == 0) *S.energy = st.sh.E;
   if (threadIdx.x == 0 && o >= 0) {
-    tally(stats, o, st.sh.flagged);
-    stats->energy = *S.energy;
+    tally(stats, o, st.sh.result_flagged);
+    stats->energy = st.sh.E;
   }
   if (o >= 0) rdf_sample(S, rdf_points(S, m, m + 1));
 }
@@ -1201,6 +1229,8 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
     if (threadIdx.x == 0) {
       S = views[r];
       st.sh.nxt_m = ~0ULL;
+      st.sh.E = *S.energy;
+      block_err() = *(volatile int*)S.err != 0;
     }
     __syncthreads();
     const unsigned long long seed = args->seeds[r];
@@ -1209,16 +1239,17 @@ __global__ void __launch_bounds__(32 * BHMC_MAX_WARPS, 2) k_batch(const SysDev* 
     loc.moves = loc.accepted = loc.rej_energy = loc.rej_domain = loc.rej_overlap = loc.rej_capacity =
         loc.flagged = 0;
     for (unsigned long long t = 0; t < args->n_moves; ++t) {
-      if (*(volatile int*)S.err) break;
+      if (block_err()) break;  // every error of the chain is raised by this block
       MoveRec* rec = args->recs ? args->recs + (size_t)r * args->n_moves + t : nullptr;
       const int o = mc_move<P, Real, LAYOUT>(S, st, args->move0 + t, (unsigned)r, key, args->step, rec,
                                              t + 1 < args->n_moves);
       if (o < 0) break;
-      if (threadIdx.x == 0) tally(&loc, o, st.sh.flagged);
+      if (threadIdx.x == 0) tally(&loc, o, st.sh.result_flagged);
       rdf_sample(S, rdf_points(S, args->move0 + t, args->move0 + t + 1));
     }
     if (threadIdx.x == 0) {
-      loc.energy = *S.energy;
+      *S.energy = st.sh.E;
+      loc.energy = st.sh.E;
       stats[r] = loc;
       if (args->errs) args->errs[r] = *(volatile int*)S.err;
     }
