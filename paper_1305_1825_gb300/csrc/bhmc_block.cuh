@@ -13,6 +13,8 @@
 #include "bhmc_traverse.cuh"
 
 #define BHMC_BSTACK 4096
+#define BHMC_PCNT_LEAF (1 << 30)  // path count entry of a leaf (never merged)
+#define BHMC_PCNT_NONE (-1)       // path count entry not yet read
 
 namespace bhmc {
 
@@ -67,12 +69,15 @@ __device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
 }
 
 // `path` (may be null) receives per point and level the cluster containing the
-// point; `leafcnt[s]` the count of point s's leaf when the traversal reaches it.
+// point, `pcnt` (with path) that cluster's charge count when internal and
+// BHMC_PCNT_LEAF for a leaf; `leafcnt[s]` the count of point s's leaf when the
+// traversal reaches it.
 // GRAD: instead of the weighted sum, accumulate the potential and its
 // gradient per role (ion point, image point).
 template <int P, typename Real, int LAYOUT, bool GRAD = false>
 __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B, unsigned pmask,
-                               int (*path)[BHMC_MAX_D + 1], int* leafcnt, TravOut& out) {
+                               int (*path)[BHMC_MAX_D + 1], int (*pcnt)[BHMC_MAX_D + 1], int* leafcnt,
+                               TravOut& out) {
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nth = blockDim.x, NW = nth >> 5, G = nth >> 3;
@@ -106,7 +111,10 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
     visited += __popc(pmask);
     if (path)
       for (int s = 0; s < 4; ++s)
-        if ((pmask >> s) & 1u) path[s][0] = 0;
+        if ((pmask >> s) & 1u) {
+          path[s][0] = 0;
+          pcnt[s][0] = rb.y;
+        }
   }
   int4 b = make_int4(-1, 0, 0, 0);
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -208,6 +216,7 @@ __device__ void block_traverse(const SysDev& S, const TravPts& T, BlockStore& B,
           const int s = __ffs(pr) - 1;
           pr &= pr - 1;
           path[s][d] = node;
+          pcnt[s][d] = fc >= 0 ? cnt : BHMC_PCNT_LEAF;
           if (fc < 0) leafcnt[s] = cnt;
         }
       }

@@ -325,8 +325,7 @@ __global__ void __launch_bounds__(256) k_commit(SysDev S, int i, double bx, doub
     sh.b[1] = by;
     sh.b[2] = bz;
   }
-  for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
-  if (threadIdx.x < 4) sh.leafcnt[threadIdx.x] = -1;
+  clear_paths(sh);
   __syncthreads();
   setup_move(S, sh);
   __syncthreads();

@@ -31,10 +31,12 @@ struct MoveSetup {
 
 struct MoveSh : MoveSetup {
   int path[4][BHMC_MAX_D + 1];
+  int pcnt[4][BHMC_MAX_D + 1];  // pre-move counts of the path clusters (BHMC_PCNT_LEAF: a leaf)
   int plen[4];
   int leafcnt[4];          // pre-move counts of the four path leaves
   int slot_i, slot_img;    // pre-move leaf slots of the ion and its image
   int merge_d[2];          // topmost level to merge on each old path
+  int may_split0;          // a new leaf exceeds the split threshold when nothing merges
   int cnt[BHMC_MAX_WARPS][5];
   int go;
   int hc_hit;              // gradient traversal: hard-core overlap at point 1
@@ -342,7 +344,10 @@ static __device__ void setup_move(const SysDev& S, MoveSetup& sh) {
 
 // Paths and path leaf counts of a move not yet found (all threads).
 __device__ __forceinline__ void clear_paths(MoveSh& sh) {
-  for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) (&sh.path[0][0])[k] = -1;
+  for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x) {
+    (&sh.path[0][0])[k] = -1;
+    (&sh.pcnt[0][0])[k] = BHMC_PCNT_NONE;
+  }
   if (threadIdx.x < 4) sh.leafcnt[threadIdx.x] = -1;
 }
 
@@ -358,7 +363,7 @@ __device__ void eval_move(const SysDev& S, MoveStore& st, bool record_path, bool
   }
   TravOut o;
   block_traverse<P, Real, LAYOUT>(S, sh.T, st.bs, sh.npts == 4 ? 15u : 3u, record_path ? sh.path : nullptr,
-                                  sh.leafcnt, o);
+                                  sh.pcnt, sh.leafcnt, o);
   if (threadIdx.x == 0) {
     const double s = o.sum + sh.fix;  // the traversal's sum and the setup's exact terms
     sh.cnt[0][0] = o.visited;
@@ -384,6 +389,12 @@ static __device__ void complete_paths(const SysDev& S, MoveSh& sh) {
     int d = 0;
     if (sh.path[s][0] < 0) sh.path[s][0] = 0;
     while (d < S.Dmax && sh.path[s][d + 1] >= 0) ++d;
+    // the clusters' counts the traversal did not record (none, as a rule)
+    for (int u = 0; u <= d; ++u)
+      if (sh.pcnt[s][u] == BHMC_PCNT_NONE) {
+        const int4 bu = S.nB[sh.path[s][u]];
+        sh.pcnt[s][u] = bu.x >= 0 ? bu.y : BHMC_PCNT_LEAF;
+      }
     if (sh.leafcnt[s] >= 0) {
       sh.plen[s] = d;
       return;
@@ -396,6 +407,7 @@ static __device__ void complete_paths(const SysDev& S, MoveSh& sh) {
       ++d;
       sh.path[s][d] = node;
       b = S.nB[node];
+      sh.pcnt[s][d] = b.x >= 0 ? b.y : BHMC_PCNT_LEAF;
     }
     sh.plen[s] = d;
     sh.leafcnt[s] = b.y;
@@ -583,6 +595,8 @@ static __device__ void commit_prep(const SysDev& S, MoveStore& st, int t0, int n
     const double q = m ? (side ? sh.qb_img : sh.qa_img) : sh.q;
     const double dx = __dsub_rn(X[0], (double)c.x), dy = __dsub_rn(X[1], (double)c.y),
                  dz = __dsub_rn(X[2], (double)c.z);
+    // the cluster's FP64 moments, which the update reads after the decision
+    prefetch_range(S.M64 + (size_t)sh.path[ps][d] * S.K, S.K * (int)sizeof(double));
     double* px = st.pw[m][side][d][0];
     double* py = st.pw[m][side][d][1];
     double* pz = st.pw[m][side][d][2];
@@ -599,9 +613,46 @@ static __device__ void commit_prep(const SysDev& S, MoveStore& st, int t0, int n
       pz[k] = vz;
     }
   }
+  // the merge test of (C) from the pre-move counts: after the move an
+  // internal cluster X at level d of an old path holds its count minus the
+  // moved charges that leave it plus those that enter it, and the topmost one
+  // at or below the split threshold merges.  One warp per moved charge, one
+  // lane per level (the tree holds at most 32 levels).
+  {
+    const int nwq = n >> 5, wq = tid >> 5, d = tid & 31;
+    for (int m = nwq - 1 - wq; m >= 0 && m < sh.nmov; m += nwq) {
+      unsigned cand = 0xffffffffu;
+      if (d <= sh.plen[2 * m] && sh.pcnt[2 * m][d] != BHMC_PCNT_LEAF) {
+        const int X = sh.path[2 * m][d];
+        int c = sh.pcnt[2 * m][d];
+        for (int u = 0; u < sh.nmov; ++u) {
+          const int na = d <= sh.plen[2 * u] ? sh.path[2 * u][d] : -1;
+          const int nb = d <= sh.plen[2 * u + 1] ? sh.path[2 * u + 1][d] : -1;
+          if (na != nb) c += (nb == X) - (na == X);
+        }
+        if (c <= S.Cs) cand = (unsigned)d;
+      }
+      const unsigned dm = __reduce_min_sync(0xffffffffu, cand);
+      if (d == 0) sh.merge_d[m] = dm == 0xffffffffu ? (1 << 20) : (int)dm;
+    }
+  }
+  // the split test of (D) when nothing merges: the new leaves' counts follow
+  // from their pre-move counts
+  if (tid == n - 3) {
+    int ms = 0;
+    for (int m = 0; m < sh.nmov; ++m) {
+      const int L = sh.path[2 * m + 1][sh.plen[2 * m + 1]];
+      int c = sh.leafcnt[2 * m + 1];
+      for (int u = 0; u < sh.nmov; ++u) {
+        const int ua = sh.path[2 * u][sh.plen[2 * u]], ub = sh.path[2 * u + 1][sh.plen[2 * u + 1]];
+        if (ua != ub) c += (ub == L) - (ua == L);
+      }
+      if (c > S.Cs) ms = 1;
+    }
+    sh.may_split0 = ms;
+  }
   if (tid == n - 1) sh.slot_i = S.slot_of[sh.i];
   if (tid == n - 2 && sh.nmov > 1) sh.slot_img = S.slot_of[sh.img];
-  if (tid < 2) sh.merge_d[tid] = 1 << 20;
 }
 
 // Index of the first of the four path clusters (old/new of the ion, old/new
@@ -691,43 +742,30 @@ static __device__ void commit_apply(const SysDev& S, MoveStore& st, int nt, int 
         if (nb >= 0) atomicAdd(count_ptr(S, nb), 1);
       }
     }
+  }
+  // commit_prep found what merges (merge_d) and whether a new leaf may split
+  // when nothing merges (may_split0); in the common case neither happens and
+  // the caller's block barrier ends the commit
+  const bool merge = sh.merge_d[0] < NL || (sh.nmov > 1 && sh.merge_d[1] < NL);
+  const bool may_split = merge || sh.may_split0 != 0;
+  if (!may_split) return;
+  team_sync(bar, nth);
+  // (C) merge the topmost internal cluster on an old path holding no more
+  // charges than the split threshold after the move
+  if (merge) {
+    if (tid == 0) {
+      const int d0 = sh.merge_d[0];
+      if (d0 < NL) merge_cluster(S, sh, sh.path[0][d0]);
+      if (sh.nmov > 1) {
+        const int d1 = sh.merge_d[1];
+        const bool inside = d0 < NL && d1 >= d0 && sh.path[2][d0] == sh.path[0][d0];
+        if (d1 < NL && !inside) merge_cluster(S, sh, sh.path[2][d1]);
+      }
+    }
     team_sync(bar, nth);
   }
-  // (C) merge the topmost internal cluster on an old path holding no more
-  // charges than the split threshold
-  for (int it = tid; it < sh.nmov * NL; it += nth) {
-    const int m = it / NL, d = it - m * NL;
-    if (d > sh.plen[2 * m]) continue;
-    const int4 b = S.nB[sh.path[2 * m][d]];
-    if (b.x >= 0 && b.y <= S.Cs) atomicMin(&sh.merge_d[m], d);
-  }
-  team_sync(bar, nth);
-  if (tid == 0) {
-    const int d0 = sh.merge_d[0];
-    if (d0 < NL) merge_cluster(S, sh, sh.path[0][d0]);
-    if (sh.nmov > 1) {
-      const int d1 = sh.merge_d[1];
-      const bool inside = d0 < NL && d1 >= d0 && sh.path[2][d0] == sh.path[0][d0];
-      if (d1 < NL && !inside) merge_cluster(S, sh, sh.path[2][d1]);
-    }
-  }
-  team_sync(bar, nth);
-  // (D) split the new leaves while they hold more charges than the split threshold.  Without a
-  // merge the new leaves' counts follow from the pre-move counts.
-  bool may_split = true;
-  if (sh.merge_d[0] >= NL && (sh.nmov < 2 || sh.merge_d[1] >= NL)) {
-    may_split = false;
-    for (int m = 0; m < sh.nmov; ++m) {
-      const int L = sh.path[2 * m + 1][sh.plen[2 * m + 1]];
-      int c = sh.leafcnt[2 * m + 1];
-      for (int u = 0; u < sh.nmov; ++u) {
-        const int ua = sh.path[2 * u][sh.plen[2 * u]], ub = sh.path[2 * u + 1][sh.plen[2 * u + 1]];
-        if (ua != ub) c += (ub == L) - (ua == L);
-      }
-      if (c > S.Cs) may_split = true;
-    }
-  }
-  for (int m = 0; m < sh.nmov && may_split; ++m) {
+  // (D) split the new leaves while they hold more charges than the split threshold
+  for (int m = 0; m < sh.nmov; ++m) {
     const int j = m ? sh.img : sh.i;
     for (int guard = 0; guard <= BHMC_MAX_D; ++guard) {
       if (tid == 0) {
@@ -942,11 +980,14 @@ template <int P, typename Real, int LAYOUT>
 __device__ bool eval_grad(const SysDev& S, MoveStore& st, unsigned pmask) {
   MoveSh& sh = st.sh;
   for (int k = threadIdx.x; k < 4 * (BHMC_MAX_D + 1); k += blockDim.x)
-    if ((pmask >> (k / (BHMC_MAX_D + 1))) & 1u) (&sh.path[0][0])[k] = -1;
+    if ((pmask >> (k / (BHMC_MAX_D + 1))) & 1u) {
+      (&sh.path[0][0])[k] = -1;
+      (&sh.pcnt[0][0])[k] = BHMC_PCNT_NONE;
+    }
   if (threadIdx.x < 4 && ((pmask >> threadIdx.x) & 1u)) sh.leafcnt[threadIdx.x] = -1;
   __syncthreads();
   TravOut o;
-  block_traverse<P, Real, LAYOUT, true>(S, sh.T, st.bs, pmask, sh.path, sh.leafcnt, o);
+  block_traverse<P, Real, LAYOUT, true>(S, sh.T, st.bs, pmask, sh.path, sh.pcnt, sh.leafcnt, o);
   if (threadIdx.x == 0) {
     for (int r = 0; r < 2; ++r) {
       sh.tphi[r] = o.phi[r];
