@@ -217,10 +217,14 @@ def test_mc_chain_plain_config(bh, oracle_mod, precision):
     assert st.energy == pytest.approx(orec["dE"][orec["outcome"] == 0].sum(), abs=1e-6 * orec["abs_sum"].max())
 
 
+@pytest.mark.parametrize("warps", [1, 4])
 @pytest.mark.parametrize("fixed_direct", [True, False])
-def test_mc_chain_colloid(bh, oracle_mod, fixed_direct):
+def test_mc_chain_colloid(bh, oracle_mod, fixed_direct, warps):
+    """The colloid chain (ion and image moved together) move by move against
+    the oracle's; one warp runs decision and commit alone (merge and split
+    tests of both moved charges in turn), four split them."""
     wl = W.colloid(n=2000, seed=10, fixed_direct=fixed_direct)
-    ctx = bh.Context(wl, warps=4)
+    ctx = bh.Context(wl, warps=warps)
     ref = _oracle(oracle_mod, wl)
     st, rec = ctx.step_mc(600, 1.0, seed=2, records=True)
     orec = ref.mc_run(2, 600)
@@ -228,7 +232,7 @@ def test_mc_chain_colloid(bh, oracle_mod, fixed_direct):
     assert ctx.export_tree() == ref.export_tree()
 
 
-@pytest.mark.parametrize("warps", [2, 8])
+@pytest.mark.parametrize("warps", [1, 2, 8])
 def test_batch_replicas_match_oracle_chains(bh, oracle_mod, warps):
     """Persistent batched chains against the oracle's; with 8 warps the next
     move's setup is computed while the current move is decided."""
