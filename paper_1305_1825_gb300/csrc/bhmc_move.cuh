@@ -569,48 +569,42 @@ __device__ __forceinline__ void team_sync(int bar, int n) {
 
 // (A0) of the local adjustment (Sec. 3.3): q (r - r_A)^k, (r - r_A)^k along
 // the old and new paths of both moved charges in FP64, one thread per
-// (charge, side, level) with the three axes' powers built by repeated
-// multiplication (the charge folded into the x powers), and the pre-move leaf
-// slots.  Threads t0 .. t0 + n - 1 run it; it reads only the move's setup and
-// its complete paths, so it may run before the Metropolis decision.
+// (charge, side, level, axis) with the powers built by repeated
+// multiplication (the charge folded into the x powers), the merge and split
+// tests, and the pre-move leaf slots.  Threads t0 .. t0 + n - 1 run it; it
+// reads only the move's setup and its complete paths, so it may run before
+// the Metropolis decision.
 static __device__ void commit_prep(const SysDev& S, MoveStore& st, int t0, int n) {
   MoveSh& sh = st.sh;
   const int P = S.p;
   const int tid = (int)threadIdx.x - t0;
   if (tid < 0 || tid >= n) return;
-  // the (path, level) items of the moved charges' paths packed on consecutive
-  // lanes: every warp that holds an item issues the whole FP64 chain, so the
-  // fewer warps hold items, the fewer FP64 instructions the move issues
+  // one lane per (path, level, axis) of the moved charges' paths, packed on
+  // consecutive lanes: each lane multiplies out one axis's powers (the
+  // charge folded into the x powers), so a lane's FP64 chain is P + 1 long
   int tot = 0;
   for (int ps = 0; ps < 2 * sh.nmov; ++ps) tot += sh.plen[ps] + 1;
-  for (int it = tid; it < tot; it += n) {
-    int ps = 0, d = it;
+  for (int it = tid; it < 3 * tot; it += n) {
+    const int ax = it % 3;
+    int ps = 0, d = it / 3;
     while (d > sh.plen[ps]) {
       d -= sh.plen[ps] + 1;
       ++ps;
     }
     const int m = ps >> 1, side = ps & 1;
-    const float4 c = S.nA[sh.path[ps][d]];
+    const int node = sh.path[ps][d];
+    const float4 c = S.nA[node];
     const double* X = m ? (side ? sh.bi : sh.ai) : (side ? sh.b : sh.a);
     const double q = m ? (side ? sh.qb_img : sh.qa_img) : sh.q;
-    const double dx = __dsub_rn(X[0], (double)c.x), dy = __dsub_rn(X[1], (double)c.y),
-                 dz = __dsub_rn(X[2], (double)c.z);
+    const double dx = __dsub_rn(X[ax], (double)(ax == 0 ? c.x : (ax == 1 ? c.y : c.z)));
     // the cluster's FP64 moments, which the update reads after the decision
-    prefetch_range(S.M64 + (size_t)sh.path[ps][d] * S.K, S.K * (int)sizeof(double));
-    double* px = st.pw[m][side][d][0];
-    double* py = st.pw[m][side][d][1];
-    double* pz = st.pw[m][side][d][2];
-    double vx = q, vy = 1.0, vz = 1.0;
-    px[0] = vx;
-    py[0] = vy;
-    pz[0] = vz;
+    if (ax == 0) prefetch_range(S.M64 + (size_t)node * S.K, S.K * (int)sizeof(double));
+    double* pw = st.pw[m][side][d][ax];
+    double v = ax == 0 ? q : 1.0;
+    pw[0] = v;
     for (int k = 1; k <= P; ++k) {
-      vx = __dmul_rn(vx, dx);
-      vy = __dmul_rn(vy, dy);
-      vz = __dmul_rn(vz, dz);
-      px[k] = vx;
-      py[k] = vy;
-      pz[k] = vz;
+      v = __dmul_rn(v, dx);
+      pw[k] = v;
     }
   }
   // the merge test of (C) from the pre-move counts: after the move an
