@@ -130,6 +130,39 @@ def test_node_pool_exhaustion_is_reported(bh):
     assert ctx.delta_energy(0, [0.0, 0.0, 0.0])[0] == bh.ESTATE
 
 
+def test_batch_pool_exhaustion_stops_the_chain(bh):
+    """Batched persistent chains whose node pool runs out: the launch stops a
+    chain at its first device error (no move runs on the tree the failed split
+    left), the call reports ENOMEM_POOL, the replica's context latches it
+    (ESTATE) and nothing faults or waits."""
+    systems = []
+    for seed in (8, 9):
+        wl = W.plain(n=300, seed=seed, C=2)
+        wl["params"]["Dmax"] = 9
+        systems.append(wl)
+    f = 0.05
+    while True:  # smallest pool both builds fit in
+        try:
+            batch = bh.Batch(systems, warps=8, layout=1, node_factor=f)
+            break
+        except bh.BhmcError as e:
+            assert e.status == bh.ENOMEM_POOL
+            f *= 1.25
+    seen = None
+    for call in range(20):
+        try:
+            batch.step_mc(1000, 3.0, [1, 2], move0=1000 * call)
+        except bh.BhmcError as e:
+            seen = e.status
+            break
+    assert seen == bh.ENOMEM_POOL
+    states = [batch.replica(r).delta_energy(0, [0.0, 0.0, 0.0])[0] for r in range(2)]
+    assert bh.ESTATE in states
+    with pytest.raises(bh.BhmcError) as e:
+        batch.step_mc(10, 3.0, [1, 2])
+    assert e.value.status == bh.ESTATE
+
+
 def test_positions_and_last_counters(bh, oracle_mod):
     """bhmc_get_positions equals the positions of bhmc_get_charges;
     bhmc_get_counters returns the last evaluation's interaction-list counters."""
